@@ -1,0 +1,258 @@
+/*
+ * omni_oracle.c -- CPU FP64 oracle for the hierarchical-grid correlator.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test-suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load this library.  It shares no code with
+ * the CUDA library: no headers, no tables, no helpers.
+ *
+ * What it computes is the plain definition of the visibilities, with no FFT:
+ *
+ *   V_c(D) = sum_t sum_{m : m, m+D in the box} x_{c,t}(m + D) * conj(x_{c,t}(m))
+ *
+ * for every 2n-D lag D with D_d in [-(n_d-1), n_d-1].  This is the
+ * convolution of the voltage hypercube with its parity-reversed copy,
+ * Eq. ConvolutionDefEq (Sec. II.C) generalised to the hypercube of
+ * Eq. ProofEq2 (Sec. II.D), with the second factor conjugated so that the
+ * result is V_ij = x_i x_j^* summed over antenna pairs with m_i - m_j = D.
+ * Sec. IV states that the hypercube algorithm yields exactly these numbers.
+ *
+ * Conventions: dimension 0 varies fastest, both in the antenna order of x and
+ * in the lag order of V; lags run from -(n_d-1) to n_d-1 along each
+ * dimension (the listings of Eqs. ConvolutionExampleEq1/2).
+ *
+ * Parity pinned by tests/test_oracle_pins.py (paper values, closed forms,
+ * invariants, a naive-DFT route and a numpy.fft route).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_MAX_DIMS 16
+
+/* Element x[i] of a [N][2] interleaved complex array of the given type. */
+static inline void load_x(const void *x, int dtype, int64_t i, double *re, double *im)
+{
+    if (dtype == 0) {                      /* complex128 */
+        const double *p = (const double *)x;
+        *re = p[2 * i];
+        *im = p[2 * i + 1];
+    } else if (dtype == 1) {               /* complex64 */
+        const float *p = (const float *)x;
+        *re = (double)p[2 * i];
+        *im = (double)p[2 * i + 1];
+    } else {                               /* complex int8 */
+        const int8_t *p = (const int8_t *)x;
+        *re = (double)p[2 * i];
+        *im = (double)p[2 * i + 1];
+    }
+}
+
+static size_t elem_bytes(int dtype) { return dtype == 0 ? 16 : dtype == 1 ? 8 : 2; }
+
+int64_t oracle_n_antennas(int D, const int32_t *n)
+{
+    int64_t N = 1;
+    for (int d = 0; d < D; ++d) N *= n[d];
+    return N;
+}
+
+int64_t oracle_n_lags(int D, const int32_t *n)
+{
+    int64_t L = 1;
+    for (int d = 0; d < D; ++d) L *= 2 * (int64_t)n[d] - 1;
+    return L;
+}
+
+/* Lag vector of lag index q (dimension 0 fastest, each from -(n_d-1)). */
+static void lag_of_index(int D, const int32_t *n, int64_t q, int32_t *lag)
+{
+    for (int d = 0; d < D; ++d) {
+        int64_t w = 2 * (int64_t)n[d] - 1;
+        lag[d] = (int32_t)(q % w) - (n[d] - 1);
+        q /= w;
+    }
+}
+
+/*
+ * Lag table: dm[q][d] = D_d and red[q] = number of antenna pairs with that
+ * 2n-D separation, prod_d (n_d - |D_d|) (the baseline distribution d = l*l^-
+ * of Sec. III for a layout map of ones).
+ */
+void oracle_lag_table(int D, const int32_t *n, int32_t *dm, int64_t *red)
+{
+    int64_t Q = oracle_n_lags(D, n);
+    for (int64_t q = 0; q < Q; ++q) {
+        int32_t lag[OR_MAX_DIMS];
+        lag_of_index(D, n, q, lag);
+        int64_t r = 1;
+        for (int d = 0; d < D; ++d) {
+            dm[q * D + d] = lag[d];
+            r *= n[d] - abs(lag[d]);
+        }
+        red[q] = r;
+    }
+}
+
+/*
+ * Antenna positions, Eq. GridEq: r = sum_k A_k (m_{2k}, m_{2k+1}), with A_k
+ * row-major 2x2 per level (level 1 first).  shape[2k], shape[2k+1] are the
+ * level-k sizes.  r is [N][2].
+ */
+void oracle_positions(int n_levels, const int32_t *shape, const double *A, double *r)
+{
+    int D = 2 * n_levels;
+    int64_t N = oracle_n_antennas(D, shape);
+    for (int64_t i = 0; i < N; ++i) {
+        int64_t rest = i;
+        double x = 0.0, y = 0.0;
+        for (int k = 0; k < n_levels; ++k) {
+            int64_t m1 = rest % shape[2 * k];
+            rest /= shape[2 * k];
+            int64_t m2 = rest % shape[2 * k + 1];
+            rest /= shape[2 * k + 1];
+            const double *a = A + 4 * k;
+            x += a[0] * (double)m1 + a[1] * (double)m2;
+            y += a[2] * (double)m1 + a[3] * (double)m2;
+        }
+        r[2 * i] = x;
+        r[2 * i + 1] = y;
+    }
+}
+
+/* Physical baseline of each lag: dr[q] = sum_k A_k (D_{2k}, D_{2k+1}). */
+void oracle_baseline_vectors(int n_levels, const double *A, int64_t Q,
+                             const int32_t *dm, double *dr)
+{
+    int D = 2 * n_levels;
+    for (int64_t q = 0; q < Q; ++q) {
+        double x = 0.0, y = 0.0;
+        for (int k = 0; k < n_levels; ++k) {
+            const double *a = A + 4 * k;
+            double d1 = dm[q * D + 2 * k], d2 = dm[q * D + 2 * k + 1];
+            x += a[0] * d1 + a[1] * d2;
+            y += a[2] * d1 + a[3] * d2;
+        }
+        dr[2 * q] = x;
+        dr[2 * q + 1] = y;
+    }
+}
+
+/*
+ * Uniqueness of the map r <-> integer indices (Sec. II.D requires every grid
+ * point to have a unique index set).  Returns 1 when two antennas lie closer
+ * than tol_rel * max|r| (or exactly coincide when max|r| is 0), else 0.
+ * Plain O(N^2) pair loop.
+ */
+int oracle_collides(int64_t N, const double *r, double tol_rel)
+{
+    double rmax = 0.0;
+    for (int64_t i = 0; i < N; ++i) {
+        double v = hypot(r[2 * i], r[2 * i + 1]);
+        if (v > rmax) rmax = v;
+    }
+    double tol = tol_rel * rmax;
+    int hit = 0;
+#pragma omp parallel for schedule(dynamic, 64) reduction(| : hit)
+    for (int64_t i = 0; i < N; ++i) {
+        for (int64_t j = i + 1; j < N; ++j) {
+            double dx = r[2 * i] - r[2 * j], dy = r[2 * i + 1] - r[2 * j + 1];
+            if (hypot(dx, dy) <= tol) hit = 1;
+        }
+    }
+    return hit;
+}
+
+/*
+ * Visibility of one lag for one channel: sum over samples t and over every
+ * lattice point m with both m and m+D inside the box of
+ * x_t(m+D) * conj(x_t(m)).  xc points at the channel's [T][N] block.
+ */
+static void one_lag(int D, const int32_t *n, const int64_t *stride, int64_t N, int64_t T,
+                    const void *xc, int dtype, const int32_t *lag, double *vre, double *vim)
+{
+    int32_t lo[OR_MAX_DIMS], hi[OR_MAX_DIMS], m[OR_MAX_DIMS];
+    int64_t shift = 0;
+    for (int d = 0; d < D; ++d) {
+        lo[d] = lag[d] < 0 ? -lag[d] : 0;          /* m_d >= 0 and m_d + D_d >= 0 */
+        hi[d] = lag[d] > 0 ? n[d] - lag[d] : n[d]; /* m_d < n_d and m_d + D_d < n_d */
+        if (hi[d] <= lo[d]) { *vre = 0.0; *vim = 0.0; return; }
+        shift += (int64_t)lag[d] * stride[d];
+    }
+    double sre = 0.0, sim = 0.0;
+    size_t eb = elem_bytes(dtype);
+    for (int64_t t = 0; t < T; ++t) {
+        const char *xt = (const char *)xc + (size_t)(t * N) * eb;
+        for (int d = 0; d < D; ++d) m[d] = lo[d];
+        for (;;) {
+            int64_t j = 0;
+            for (int d = 0; d < D; ++d) j += (int64_t)m[d] * stride[d];
+            double ar, ai, br, bi;
+            load_x(xt, dtype, j + shift, &ar, &ai);   /* x(m + D) */
+            load_x(xt, dtype, j, &br, &bi);           /* x(m)     */
+            sre += ar * br + ai * bi;                 /* a * conj(b) */
+            sim += ai * br - ar * bi;
+            int d = 0;
+            while (d < D) {
+                if (++m[d] < hi[d]) break;
+                m[d] = lo[d];
+                ++d;
+            }
+            if (d == D) break;
+        }
+    }
+    *vre = sre;
+    *vim = sim;
+}
+
+/*
+ * Full brute-force correlator.  x is [C][T][N] complex of type dtype
+ * (0 = complex128, 1 = complex64, 2 = complex int8); V is [C][Q][2] with
+ * Q = prod_d (2 n_d - 1).  Parallel over lags.
+ */
+void oracle_correlate(int D, const int32_t *n, int64_t C, int64_t T, int dtype,
+                      const void *x, double *V)
+{
+    int64_t N = oracle_n_antennas(D, n);
+    int64_t Q = oracle_n_lags(D, n);
+    int64_t stride[OR_MAX_DIMS];
+    int64_t s = 1;
+    for (int d = 0; d < D; ++d) { stride[d] = s; s *= n[d]; }
+    size_t eb = elem_bytes(dtype);
+    for (int64_t c = 0; c < C; ++c) {
+        const char *xc = (const char *)x + (size_t)(c * T * N) * eb;
+#pragma omp parallel for schedule(dynamic, 16)
+        for (int64_t q = 0; q < Q; ++q) {
+            int32_t lag[OR_MAX_DIMS];
+            lag_of_index(D, n, q, lag);
+            one_lag(D, n, stride, N, T, xc, dtype, lag, &V[2 * (c * Q + q)],
+                    &V[2 * (c * Q + q) + 1]);
+        }
+    }
+}
+
+/*
+ * The same definition evaluated only at selected (channel, lag) pairs:
+ * chan[s], lag_index[s] for s < S; V is [S][2].  Used for sampled checks at
+ * sizes where the full N^2 sum is out of reach.
+ */
+void oracle_correlate_selected(int D, const int32_t *n, int64_t C, int64_t T, int dtype,
+                               const void *x, int64_t S, const int64_t *chan,
+                               const int64_t *lag_index, double *V)
+{
+    int64_t N = oracle_n_antennas(D, n);
+    int64_t stride[OR_MAX_DIMS];
+    int64_t s = 1;
+    for (int d = 0; d < D; ++d) { stride[d] = s; s *= n[d]; }
+    size_t eb = elem_bytes(dtype);
+    (void)C;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t k = 0; k < S; ++k) {
+        int32_t lag[OR_MAX_DIMS];
+        lag_of_index(D, n, lag_index[k], lag);
+        const char *xc = (const char *)x + (size_t)(chan[k] * T * N) * eb;
+        one_lag(D, n, stride, N, T, xc, dtype, lag, &V[2 * k], &V[2 * k + 1]);
+    }
+}
+
+int oracle_max_dims(void) { return OR_MAX_DIMS; }

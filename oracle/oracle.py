@@ -1,0 +1,167 @@
+"""Python entry points of the CPU FP64 oracle (a ctypes wrapper over omni_oracle.c).
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, by __graft_entry__.smoke() and by
+bench.py's CPU-baseline leg, never by the product package.
+
+What the oracle computes is the plain brute-force definition of the summed
+visibilities (Eq. ConvolutionDefEq, Sec. II.C; Eq. ProofEq2, Sec. II.D):
+V_c(D) = sum_t sum_m x_{c,t}(m+D) conj(x_{c,t}(m)), plus the lag table with
+its redundancy counts (Sec. III) and the geometry of Eq. GridEq.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from typing import Sequence, Tuple
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "omni_oracle.c")
+_LIBDIR = os.path.join(_HERE, "lib")
+_LIB = os.path.join(_LIBDIR, "libomni_oracle.so")
+
+DTYPE_CODE = {"cf64": 0, "cf32": 1, "ci8": 2}
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (-O2, OpenMP) into oracle/lib/."""
+    os.makedirs(_LIBDIR, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB)
+        i32p = ctypes.POINTER(ctypes.c_int32)
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        f64p = ctypes.POINTER(ctypes.c_double)
+        L.oracle_n_antennas.restype = ctypes.c_int64
+        L.oracle_n_antennas.argtypes = [ctypes.c_int, i32p]
+        L.oracle_n_lags.restype = ctypes.c_int64
+        L.oracle_n_lags.argtypes = [ctypes.c_int, i32p]
+        L.oracle_lag_table.restype = None
+        L.oracle_lag_table.argtypes = [ctypes.c_int, i32p, i32p, i64p]
+        L.oracle_positions.restype = None
+        L.oracle_positions.argtypes = [ctypes.c_int, i32p, f64p, f64p]
+        L.oracle_baseline_vectors.restype = None
+        L.oracle_baseline_vectors.argtypes = [ctypes.c_int, f64p, ctypes.c_int64, i32p, f64p]
+        L.oracle_collides.restype = ctypes.c_int
+        L.oracle_collides.argtypes = [ctypes.c_int64, f64p, ctypes.c_double]
+        L.oracle_correlate.restype = None
+        L.oracle_correlate.argtypes = [ctypes.c_int, i32p, ctypes.c_int64, ctypes.c_int64,
+                                       ctypes.c_int, ctypes.c_void_p, f64p]
+        L.oracle_correlate_selected.restype = None
+        L.oracle_correlate_selected.argtypes = [ctypes.c_int, i32p, ctypes.c_int64,
+                                                ctypes.c_int64, ctypes.c_int, ctypes.c_void_p,
+                                                ctypes.c_int64, i64p, i64p, f64p]
+        L.oracle_max_dims.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _i32(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.int32))
+
+
+def _ptr(a: np.ndarray, ct):
+    return a.ctypes.data_as(ctypes.POINTER(ct))
+
+
+def n_lags(dims: Sequence[int]) -> int:
+    d = _i32(dims)
+    return int(lib().oracle_n_lags(len(d), _ptr(d, ctypes.c_int32)))
+
+
+def lag_table(dims: Sequence[int]) -> Tuple[np.ndarray, np.ndarray]:
+    """(dm [Q][D] int32, redundancy [Q] int64), dimension 0 fastest."""
+    d = _i32(dims)
+    Q = n_lags(d)
+    dm = np.zeros((Q, len(d)), dtype=np.int32)
+    red = np.zeros(Q, dtype=np.int64)
+    lib().oracle_lag_table(len(d), _ptr(d, ctypes.c_int32), _ptr(dm, ctypes.c_int32),
+                           _ptr(red, ctypes.c_int64))
+    return dm, red
+
+
+def _level_arrays(levels) -> Tuple[np.ndarray, np.ndarray]:
+    shape = _i32([v for lv in levels for v in (lv.n1, lv.n2)])
+    A = np.ascontiguousarray(np.array([lv.A for lv in levels], dtype=np.float64).ravel())
+    return shape, A
+
+
+def positions(levels) -> np.ndarray:
+    shape, A = _level_arrays(levels)
+    N = int(np.prod(shape))
+    r = np.zeros((N, 2))
+    lib().oracle_positions(len(levels), _ptr(shape, ctypes.c_int32), _ptr(A, ctypes.c_double),
+                           _ptr(r, ctypes.c_double))
+    return r
+
+
+def baseline_vectors(levels, dm: np.ndarray) -> np.ndarray:
+    _, A = _level_arrays(levels)
+    dm = np.ascontiguousarray(dm, dtype=np.int32)
+    dr = np.zeros((dm.shape[0], 2))
+    lib().oracle_baseline_vectors(len(levels), _ptr(A, ctypes.c_double), dm.shape[0],
+                                  _ptr(dm, ctypes.c_int32), _ptr(dr, ctypes.c_double))
+    return dr
+
+
+def collides(levels, tol_rel: float = 1e-9) -> bool:
+    r = np.ascontiguousarray(positions(levels))
+    return bool(lib().oracle_collides(r.shape[0], _ptr(r, ctypes.c_double), tol_rel))
+
+
+def _as_input(x) -> Tuple[np.ndarray, int]:
+    """Accept a [C][T][N][2] array (float64/float32/int8) or complex [C][T][N]."""
+    a = x.numpy() if hasattr(x, "numpy") else np.asarray(x)
+    if np.iscomplexobj(a):
+        a = np.stack([a.real, a.imag], axis=-1).astype(np.float64)
+    a = np.ascontiguousarray(a)
+    if a.dtype == np.float64:
+        return a, 0
+    if a.dtype == np.float32:
+        return a, 1
+    if a.dtype == np.int8:
+        return a, 2
+    raise TypeError(f"unsupported voltage dtype {a.dtype}")
+
+
+def correlate(dims: Sequence[int], x) -> np.ndarray:
+    """Brute-force visibilities, complex128 [C][Q] (lags dimension-0 fastest)."""
+    d = _i32(dims)
+    a, code = _as_input(x)
+    C, T, N = a.shape[0], a.shape[1], a.shape[2]
+    if N != int(np.prod(d)):
+        raise ValueError("voltage length does not match the lattice")
+    Q = n_lags(d)
+    V = np.zeros((C, Q, 2))
+    lib().oracle_correlate(len(d), _ptr(d, ctypes.c_int32), C, T, code,
+                           a.ctypes.data_as(ctypes.c_void_p), _ptr(V, ctypes.c_double))
+    return V[..., 0] + 1j * V[..., 1]
+
+
+def correlate_selected(dims: Sequence[int], x, chans, lag_idx) -> np.ndarray:
+    """Brute-force visibilities at selected (channel, lag index) pairs, complex128 [S]."""
+    d = _i32(dims)
+    a, code = _as_input(x)
+    C, T = a.shape[0], a.shape[1]
+    ch = np.ascontiguousarray(np.asarray(chans, dtype=np.int64))
+    lq = np.ascontiguousarray(np.asarray(lag_idx, dtype=np.int64))
+    V = np.zeros((len(ch), 2))
+    lib().oracle_correlate_selected(len(d), _ptr(d, ctypes.c_int32), C, T, code,
+                                    a.ctypes.data_as(ctypes.c_void_p), len(ch),
+                                    _ptr(ch, ctypes.c_int64), _ptr(lq, ctypes.c_int64),
+                                    _ptr(V, ctypes.c_double))
+    return V[:, 0] + 1j * V[:, 1]

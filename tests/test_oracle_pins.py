@@ -1,0 +1,273 @@
+"""Pins for the CPU FP64 oracle, each tied to something other than the oracle.
+
+Every check here runs on the CPU.  The oracle is the brute-force definition of
+the summed visibilities (Eq. ConvolutionDefEq / ProofEq2); these tests hold it
+to the values the paper prints, to closed forms, to invariants, and to two
+independent routes (a naive O(L^2) DFT and numpy.fft) that reach the same
+numbers through the zero-padded FFT / square / inverse-FFT procedure of
+Sec. II.C.
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+from conftest import read_golden
+from oracle import oracle
+from paper_0909_0001_gb300 import synth
+
+
+def _cplx(x):
+    x = np.asarray(x, dtype=np.float64)
+    return x[..., 0] + 1j * x[..., 1]
+
+
+def _lags_per_dim(dims):
+    return [np.arange(-(n - 1), n) for n in dims]
+
+
+def _lag_vectors(dims):
+    """All lag vectors, dimension 0 fastest (written independently of the oracle)."""
+    rev = list(itertools.product(*[range(-(n - 1), n) for n in dims[::-1]]))
+    return np.array([v[::-1] for v in rev], dtype=np.int64)
+
+
+def fft_route(dims, x):
+    """Sec. II.C: zero-pad to 2n_d, FFT, |.|^2, sum over t, inverse FFT, gather lags."""
+    x = _cplx(x) if not np.iscomplexobj(x) else x
+    C, T, N = x.shape
+    shape_rev = tuple(dims[::-1])                    # numpy axis order: slowest first
+    pad = tuple(2 * n if n > 1 else 1 for n in shape_rev)
+    out = []
+    for c in range(C):
+        P = np.zeros(pad)
+        for t in range(T):
+            F = np.fft.fftn(x[c, t].reshape(shape_rev), s=pad, axes=tuple(range(len(pad))))
+            P += np.abs(F) ** 2
+        g = np.fft.ifftn(P)
+        idx = np.ix_(*[np.arange(-(n - 1), n) % L for n, L in zip(shape_rev, pad)])
+        out.append(g[idx].ravel())
+    return np.array(out)
+
+
+def naive_dft_route(dims, x):
+    """The same route with the multidimensional DFT written as an explicit O(L^2) sum."""
+    x = _cplx(x)
+    C, T, N = x.shape
+    Ls = [2 * n if n > 1 else 1 for n in dims]
+    L = int(np.prod(Ls))
+    # flattened lattice coordinates, dimension 0 fastest
+    kk = np.array(list(itertools.product(*[range(l) for l in Ls[::-1]])))[:, ::-1]
+    mm = np.array(list(itertools.product(*[range(n) for n in dims[::-1]])))[:, ::-1]
+    phase = np.zeros((L, N))
+    for d, Ld in enumerate(Ls):
+        phase += np.outer(kk[:, d], mm[:, d]) / Ld
+    W = np.exp(-2j * math.pi * phase)                 # forward DFT, e^{-}
+    lags = _lag_vectors(dims)
+    phase_inv = np.zeros((len(lags), L))
+    for d, Ld in enumerate(Ls):
+        phase_inv += np.outer(lags[:, d], kk[:, d]) / Ld
+    Winv = np.exp(2j * math.pi * phase_inv) / L        # inverse DFT, e^{+}, 1/L
+    out = []
+    for c in range(C):
+        P = np.zeros(L)
+        for t in range(T):
+            P += np.abs(W @ x[c, t]) ** 2
+        out.append(Winv @ P)
+    return np.array(out)
+
+
+def relerr(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+# ---------------------------------------------------------------- paper values
+
+def test_warmup_example_1d():
+    g = read_golden("warmup_example.txt")
+    f = g["voltages"][0]
+    x = np.zeros((1, 1, 9, 2))
+    x[0, 0, [0, 1, 2, 6, 7, 8], 0] = f                 # x = 1,2,3,7,8,9
+    V = oracle.correlate([9, 1], x)
+    np.testing.assert_array_equal(V.real[0], g["g_1d"][0])
+    np.testing.assert_array_equal(V.imag[0], 0.0)
+
+
+def test_warmup_example_two_level():
+    g = read_golden("warmup_example.txt")
+    x = np.zeros((1, 1, 6, 2))
+    x[0, 0, :, 0] = g["voltages"][0]
+    dims = synth.lattice_dims(synth.paper_fixture("warmup_2level"))
+    assert dims == [3, 1, 2, 1]
+    V = oracle.correlate(dims, x)[0]
+    np.testing.assert_array_equal(V.real.reshape(3, 5), np.array(g["G_2d_row"]))
+    # Mapping the 2-D lag (D1, D2) to the physical separation D1 + 6 D2 gives
+    # back the 17-long 1-D result (zeros at the separations no pair has).
+    dm, _ = oracle.lag_table(dims)
+    g1 = np.zeros(17)
+    for q in range(len(V)):
+        g1[dm[q, 0] + 6 * dm[q, 2] + 8] += V[q].real
+    np.testing.assert_array_equal(g1, g["g_1d"][0])
+
+
+# ---------------------------------------------------------------- closed forms
+
+@pytest.mark.parametrize("dims", [[4, 1], [3, 5], [4, 3, 2, 3], [2, 3, 1, 2, 3, 2]])
+def test_all_ones_gives_redundancy(dims):
+    T = 3
+    x = synth.all_ones(dims, 1, T)
+    V = oracle.correlate(dims, x)[0]
+    lags = _lag_vectors(dims)
+    expect = T * np.prod([n - np.abs(lags[:, d]) for d, n in enumerate(dims)], axis=0)
+    np.testing.assert_array_equal(V.real, expect)
+    np.testing.assert_array_equal(V.imag, 0.0)
+    dm, red = oracle.lag_table(dims)
+    np.testing.assert_array_equal(dm, lags)
+    np.testing.assert_array_equal(red * T, expect)
+
+
+def test_redundancy_counts_by_pair_enumeration():
+    """Redundancy of each lag counted by visiting every antenna pair."""
+    dims = [3, 2, 2, 3]
+    m = synth.antenna_indices([synth.Level(3, 2), synth.Level(2, 3)])
+    lags = _lag_vectors(dims)
+    count = {tuple(v): 0 for v in lags}
+    for i in range(len(m)):
+        for j in range(len(m)):
+            count[tuple(m[i] - m[j])] += 1
+    _, red = oracle.lag_table(dims)
+    np.testing.assert_array_equal(red, [count[tuple(v)] for v in lags])
+
+
+def test_single_antenna_delta():
+    dims = [3, 4, 2, 2]
+    N = int(np.prod(dims))
+    T = 5
+    a = np.array([0.75, -1.25])
+    x = np.zeros((1, T, N, 2))
+    x[0, :, 17] = a
+    V = oracle.correlate(dims, x)[0]
+    zero = len(V) // 2                                 # lag 0 sits in the middle
+    assert _lag_vectors(dims)[zero].tolist() == [0, 0, 0, 0]
+    assert V[zero] == pytest.approx(T * (a @ a))
+    V[zero] = 0
+    assert np.all(V == 0)
+
+
+def test_plane_wave_closed_form():
+    """x_t(i) = a_t exp(2 pi i u.r_i):  V(D) = sum|a_t|^2 exp(2 pi i u.dr(D)) prod(n_d-|D_d|)."""
+    levels = synth.hierarchy([(4, 3), (3, 2)], [0.3, 1.1], [0.1, -0.25])
+    dims = synth.lattice_dims(levels)
+    r = synth.antenna_positions(levels)
+    u = np.array([0.137, -0.291])
+    rng = np.random.default_rng(5)
+    a = rng.normal(size=4) + 1j * rng.normal(size=4)
+    x = a[:, None] * np.exp(2j * math.pi * (r @ u))[None, :]
+    V = oracle.correlate(dims, x[None])[0]
+    lags = _lag_vectors(dims)
+    dr = np.zeros((len(lags), 2))
+    for k, lv in enumerate(levels):
+        dr += lags[:, 2 * k:2 * k + 2] @ np.asarray(lv.A).reshape(2, 2).T
+    red = np.prod([n - np.abs(lags[:, d]) for d, n in enumerate(dims)], axis=0)
+    expect = np.sum(np.abs(a) ** 2) * np.exp(2j * math.pi * (dr @ u)) * red
+    assert relerr(V, expect) < 1e-13
+
+
+# ---------------------------------------------------------------- invariants
+
+def test_hermitian_parseval_dc():
+    dims = [4, 3, 3, 2]
+    x = synth.random_complex(dims, 2, 3, seed=11).numpy().astype(np.float64)
+    V = oracle.correlate(dims, x)
+    xc = _cplx(x)
+    for c in range(2):
+        # Hermitian: V(-D) = conj V(D)  (Sec. II.C palindrome for real input)
+        np.testing.assert_allclose(V[c][::-1], np.conj(V[c]), rtol=0, atol=1e-12)
+        zero = V.shape[1] // 2
+        assert V[c, zero].real == pytest.approx(np.sum(np.abs(xc[c]) ** 2), rel=1e-13)
+        assert abs(V[c, zero].imag) < 1e-12
+        assert np.sum(V[c]) == pytest.approx(np.sum(np.abs(xc[c].sum(axis=1)) ** 2), rel=1e-12)
+
+
+# ---------------------------------------------------------------- other routes
+
+@pytest.mark.parametrize("dims", [[2, 2, 2, 2], [3, 2, 2, 1], [4, 3], [1, 3, 2, 1]])
+def test_naive_dft_route(dims):
+    x = synth.random_complex(dims, 2, 2, seed=3).numpy().astype(np.float64)
+    assert relerr(oracle.correlate(dims, x), naive_dft_route(dims, x)) < 1e-12
+
+
+@pytest.mark.parametrize("fixture", ["three_level", "blocks", "interleaved", "warmup_2level"])
+def test_numpy_fft_route_on_paper_layouts(fixture):
+    levels = synth.paper_fixture(fixture)
+    dims = synth.lattice_dims(levels)
+    T = 2 if fixture != "blocks" else 1
+    x = synth.random_complex(dims, 1, T, seed=7).numpy().astype(np.float64)
+    assert relerr(oracle.correlate(dims, x), fft_route(dims, x)) < 1e-12
+
+
+def test_numpy_fft_route_medium():
+    dims = [6, 4, 3, 5]
+    x = synth.random_complex(dims, 2, 3, seed=9).numpy().astype(np.float64)
+    assert relerr(oracle.correlate(dims, x), fft_route(dims, x)) < 1e-12
+
+
+# ---------------------------------------------------------------- input types
+
+def test_input_types_are_converted_exactly():
+    dims = [4, 4, 2, 3]
+    x8 = synth.random_complex(dims, 2, 2, seed=1, dtype="ci8", sigma=40.0)
+    ref = oracle.correlate(dims, x8.numpy().astype(np.float64))
+    np.testing.assert_array_equal(oracle.correlate(dims, x8), ref)
+    np.testing.assert_array_equal(oracle.correlate(dims, x8.float()), ref)
+
+
+def test_selected_lags_match_full():
+    dims = [5, 3, 2, 2]
+    x = synth.random_complex(dims, 3, 2, seed=2)
+    V = oracle.correlate(dims, x)
+    rng = np.random.default_rng(0)
+    ch = rng.integers(0, 3, 40)
+    q = rng.integers(0, V.shape[1], 40)
+    np.testing.assert_array_equal(oracle.correlate_selected(dims, x, ch, q), V[ch, q])
+
+
+# ---------------------------------------------------------------- geometry
+
+def test_positions_match_generator_geometry():
+    levels = synth.paper_fixture("three_level")
+    np.testing.assert_allclose(oracle.positions(levels), synth.antenna_positions(levels),
+                               rtol=0, atol=1e-12)
+    # Fig. 1 numbers: antenna i_1 = 4, i_4 = 2 of block (0,0,0,0) sits at (4, 2);
+    # level-2 step a_2 = (8, 0), a_5 = (2, 8); level-3 step a_3 = (40, 10), a_6 = (-10, 40)
+    r = oracle.positions(levels)
+    assert r[4 + 5 * 2].tolist() == [4.0, 2.0]
+    assert r[15].tolist() == [8.0, 0.0]                  # m = (0,0,1,0,0,0)
+    assert r[15 * 3].tolist() == [2.0, 8.0]              # m = (0,0,0,1,0,0)
+    assert r[15 * 9].tolist() == [40.0, 10.0]            # m = (0,0,0,0,1,0)
+    assert r[15 * 27].tolist() == [-10.0, 40.0]          # m = (0,0,0,0,0,1)
+
+
+def test_baseline_vectors():
+    levels = synth.hierarchy([(3, 2), (2, 3)], [0.4, 2.0], [0.2, -0.1])
+    dims = synth.lattice_dims(levels)
+    dm, _ = oracle.lag_table(dims)
+    dr = oracle.baseline_vectors(levels, dm)
+    r = synth.antenna_positions(levels)
+    m = synth.antenna_indices(levels)
+    lut = {tuple(v): i for i, v in enumerate(m)}
+    for q in range(len(dm)):
+        for i, mi in enumerate(m):
+            j = lut.get(tuple(mi - dm[q]))
+            if j is not None:                            # pair (i, j) has m_i - m_j = D
+                np.testing.assert_allclose(dr[q], r[i] - r[j], atol=1e-12)
+                break
+
+
+def test_collision_check():
+    assert not oracle.collides(synth.paper_fixture("interleaved"))
+    assert not oracle.collides(synth.paper_fixture("three_level"))
+    # a_1 = (1,0) with 4 points and a_2 = (2,0) with 2 points put two antennas at x = 2, 3
+    clash = [synth.Level(4, 1, (1.0, 0.0, 0.0, 1.0)), synth.Level(2, 1, (2.0, 0.0, 0.0, 1.0))]
+    assert oracle.collides(clash)
