@@ -1,0 +1,363 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the hierarchical-grid FFT correlator on GB300.
+
+One step = one pass of the whole hot path over one batch of synthetic input:
+omni_correlate over C channels x T samples (scatter, forward 2n-D FFT, |F|^2
+time integration) followed by omni_visibilities (inverse 2n-D FFT, 1/L,
+lag gather) with the accumulator reset.  Metric: antenna-samples per second
+(N x T x C per step).  The default workload is the 2-level 16x16 / 8x8
+hierarchy (N = 16384, 64 channels x 1024 samples of int8 voltages, 2.1 GB per
+step, larger than L2, so no flush is needed between steps).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU runs (torchrun, one rank per GPU) are independent replicas: the
+channels of different ranks never interact, so there is no collective on the
+data path and the result scales weakly.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "antenna-samples/s"
+UNIT = "antenna*samples/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="hier2")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "mixed"])
+    ap.add_argument("--channels", type=int, default=None,
+                    help="run a smaller case of the workload (profiling)")
+    ap.add_argument("--samples", type=int, default=None,
+                    help="run a smaller case of the workload (profiling)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+def workload_config(w, precision):
+    return {
+        "workload": f"{w.name}: {w.description}",
+        "levels": [[lv.n1, lv.n2] for lv in w.levels],
+        "antennas": w.n_antennas,
+        "channels": w.channels,
+        "samples": w.samples,
+        "input": w.dtype,
+        "precision": precision,
+        "l2": "inputs larger than L2 (%.2f GB of voltages per step); no flush"
+              % (w.n_antennas * w.channels * w.samples * (2 if w.dtype == "ci8" else 8) / 1e9),
+    }
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.out, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.out.close()
+
+    def summary(self):
+        if self.proc is None or not self.path:
+            return None
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                p = [v.strip() for v in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    sm.append(float(p[1]))
+                    smax = float(p[2])
+                except ValueError:
+                    continue
+                for n, v in zip(names, p[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ roofline
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs"), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    from paper_0909_0001_gb300.build import CSRC
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(CSRC)):
+        if f.endswith((".cu", ".cuh", ".h", ".cpp")):
+            with open(os.path.join(CSRC, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel_name, workload):
+    """DRAM bytes per launch from a committed ncu summary, if it matches this build."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    want = kernel_source_hash()
+    with open(path) as f:
+        for line in f:
+            p = line.strip().split("|")
+            if len(p) >= 4 and p[0].strip() == workload and p[1].strip() == kernel_name \
+                    and p[2].strip() == want:
+                try:
+                    return float(p[3])
+                except ValueError:
+                    return None
+    return None
+
+
+def roofline(stats, workload):
+    timed = [s for s in stats if s["launches"] > 0 and s["total_ms"] > 0]
+    if not timed:
+        return None
+    top = max(timed, key=lambda s: s["total_ms"])
+    peak, kind = measured_peaks()
+    avg_ms = top["total_ms"] / top["launches"]
+    bytes_per_launch = top["bytes"] / top["launches"]
+    achieved = bytes_per_launch / (avg_ms * 1e-3) / 1e9
+    traffic = recorded_traffic(top["name"], workload)
+    total = sum(s["total_ms"] for s in timed)
+    return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": traffic,
+            "kernel": top["name"], "peak_kind": kind,
+            "bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_ms,
+            "share_of_kernel_time": round(top["total_ms"] / total, 4)}
+
+
+# ------------------------------------------------------------------ CPU oracle
+
+def oracle_rate(w, x_host, target_s=15.0, max_samples=64):
+    """Time the oracle as it stands on channel 0's first samples; antenna-samples/s."""
+    from oracle import oracle
+    dims = w.dims
+    lib = oracle.lib()
+    try:
+        import ctypes
+        lib.oracle_num_threads.restype = ctypes.c_int
+        cores = int(lib.oracle_num_threads())
+    except AttributeError:
+        cores = os.cpu_count()
+    ts = 1
+    t0 = time.perf_counter()
+    oracle.correlate(dims, x_host[0:1, 0:ts])
+    dt = time.perf_counter() - t0
+    ts = int(max(1, min(max_samples, x_host.shape[1], target_s / max(dt, 1e-3))))
+    t0 = time.perf_counter()
+    oracle.correlate(dims, x_host[0:1, 0:ts])
+    dt = time.perf_counter() - t0
+    units = w.n_antennas * ts
+    return units / dt, cores, f"channel 0, first {ts} samples ({units} antenna-samples), {dt:.1f} s"
+
+
+# ------------------------------------------------------------------ arms
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    from paper_0909_0001_gb300 import synth
+    w = synth.workload(args.workload)
+    x = synth.voltages(w, channels=1, samples=64)
+    per_step = max(5.0, 150.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        oracle_rate(w, x, target_s=per_step)
+    rates, cores, sample = [], None, ""
+    for _ in range(args.steps):
+        r, cores, sample = oracle_rate(w, x, target_s=per_step)
+        rates.append(r)
+    value = statistics.mean(rates)
+    ms = w.n_antennas * w.samples * w.channels / value * 1e3
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": workload_config(w, "fp64 oracle"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample + " per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_0909_0001_gb300 import omni, synth
+
+    rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    w = synth.workload(args.workload)
+    if args.channels:
+        w.channels = args.channels
+    if args.samples:
+        w.samples = args.samples
+    units = w.n_antennas * w.samples * w.channels
+    x = synth.voltages(w, device="cuda", seed=w.seed + 7919 * rank)
+    plan = omni.Plan(w.levels, w.channels, dtype=w.dtype, precision=args.precision)
+    vis = torch.empty((w.channels, plan.n_lags), dtype=torch.complex128, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        plan.correlate(x)
+        plan.visibilities(reset=True, out=vis)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    plan.kernel_stats(clear=True)
+    plan.profile(True)
+
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    plan.profile(False)
+    ms = e0.elapsed_time(e1) / args.steps
+    stats = plan.kernel_stats(clear=True)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * units / (ms * 1e-3)
+    launches = sum(s["launches"] for s in stats)
+
+    # end to end through the host-buffer entry points
+    e2e = None
+    if not args.no_e2e:
+        xh = x.cpu().pin_memory()
+        vh = torch.empty((w.channels, plan.n_lags), dtype=torch.complex128).pin_memory()
+        plan.correlate_host(xh)
+        plan.visibilities_host(reset=True, out=vh)
+        n_e2e = max(1, min(args.steps, 3))
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            plan.correlate_host(xh)
+            plan.visibilities_host(reset=True, out=vh)
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / n_e2e
+        if world > 1:
+            t = torch.tensor([dt], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": world * units / dt, "unit": UNIT,
+               "h2d_bytes_per_step": xh.numel() * xh.element_size(),
+               "d2h_bytes_per_step": vh.numel() * vh.element_size(),
+               "ms_per_step": dt * 1e3, "steps": n_e2e}
+        del xh, vh
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        r, cores, sample = oracle_rate(w, x[0:1, 0:64].cpu())
+        cpu = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic",
+                "config": dict(workload_config(w, args.precision),
+                               parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
+                "roofline": roofline(stats, args.workload),
+                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clk.summary(),
+                "kernels": [{k: s[k] for k in ("name", "launches", "total_ms")}
+                            for s in stats if s["launches"]]}
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

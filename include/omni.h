@@ -1,0 +1,172 @@
+/*
+ * omni.h -- C ABI of the GB300 hierarchical-grid ("hypercube") FFT correlator.
+ *
+ * The method (Tegmark & Zaldarriaga, "Omniscopes", Sec. II): antennas sit on
+ * an n-level hierarchical grid r = sum_k A_k m_k (Eq. GridEq).  Placing the
+ * voltages f_r of one time sample and frequency channel in the 2n-D hypercube
+ * F_{i1 i2 ...} (Eq. ProofEq2), zero-padding it, taking the 2n-D FFT, squaring
+ * the modulus, summing over time and inverse-transforming gives G, the
+ * visibilities summed over every antenna pair with the same 2n-D separation
+ * (Sec. II.C: "zero-padded FFT, squaring the result and inverse transforming").
+ *
+ * Conventions (all entry points):
+ *  - A hierarchy is given as n_levels omni_level records, level 1 (finest)
+ *    first.  The lattice has D = 2 n_levels dimensions with sizes
+ *    (n1 of level 1, n2 of level 1, n1 of level 2, ...); dimension 0 varies
+ *    fastest.
+ *  - Voltages are [C][T][N] complex values, interleaved (re, im), N = prod n_d,
+ *    antenna index row-major with dimension 0 fastest, i.e. antenna i has
+ *    m_0 = i mod n_0, m_1 = (i / n_0) mod n_1, ...
+ *  - Lags: each dimension d runs D_d = -(n_d-1) .. n_d-1, dimension 0 fastest;
+ *    Q = prod_d (2 n_d - 1) lags per channel.  The visibility of lag D is
+ *    V(D) = sum_t sum_m x_t(m + D) conj(x_t(m)), i.e. V_ij = x_i x_j^* summed
+ *    over all pairs with m_i - m_j = D (the conjugate is the complex-voltage
+ *    reading of Eq. ConvolutionDefEq, which the paper writes for real f).
+ *  - The forward transform uses exp(-2 pi i k.m / L), the padded length is
+ *    L_d = 2 n_d (1 when n_d = 1), and the output is normalised by 1/L only
+ *    once, in the inverse transform; visibilities are summed, not averaged,
+ *    over time.
+ *  - Every call returns an omni_status; omni_last_error() gives a message for
+ *    the calling thread's last failure.  Device work is asynchronous on the
+ *    stream passed in (a cudaStream_t passed as void*, NULL = legacy default
+ *    stream); a device-side failure is reported by the next call that
+ *    synchronises (omni_visibilities*) or by omni_sync.
+ *  - Nothing here frees or retains memory owned by the caller.
+ */
+#ifndef OMNI_H
+#define OMNI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* One level of the hierarchy (Eq. GridEq): an n1 x n2 block placed by the
+ * row-major 2x2 matrix A = [a_k | a_{k+n}] (the level's two lattice vectors as
+ * columns), r = A (m1, m2)^T.  Sec. II.D numbers the first axes a_1..a_n and
+ * the second axes a_{n+1}..a_{2n}. */
+typedef struct omni_level {
+    int32_t n1;
+    int32_t n2;
+    double A[4];
+} omni_level;
+
+typedef enum omni_status {
+    OMNI_OK = 0,
+    OMNI_ERR_INVALID_ARG = 1,  /* null pointer, non-positive size, bad enum */
+    OMNI_ERR_COLLISION = 2,    /* two antennas coincide: the map r -> (m_k) is
+                                  not unique, which Sec. II.D requires */
+    OMNI_ERR_UNSUPPORTED = 3,  /* a size this build does not handle */
+    OMNI_ERR_OOM = 4,          /* device or pinned-host allocation failed */
+    OMNI_ERR_CUDA = 5,         /* a CUDA runtime call or kernel failed */
+    OMNI_ERR_TIMEOUT = 6       /* a bounded device-side wait gave up */
+} omni_status;
+
+typedef enum omni_dtype {
+    OMNI_IN_CF32 = 0,  /* float re, float im (8 bytes per antenna-sample) */
+    OMNI_IN_CI8 = 1    /* int8 re, int8 im (2 bytes), values in [-127, 127] */
+} omni_dtype;
+
+typedef enum omni_precision {
+    OMNI_FP32 = 0,       /* all FFT arithmetic in FP32 */
+    OMNI_MIXED_FP16 = 1  /* DFT stages as split FP16 tensor-core GEMMs */
+} omni_precision;
+
+typedef struct omni_plan omni_plan;
+
+/* Lattice sizes of a hierarchy without creating a plan (host only, no GPU).
+ * n_antennas = prod n_d, n_lags = prod (2 n_d - 1). */
+omni_status omni_lattice_shape(const omni_level* levels, int n_levels,
+                               int64_t* n_antennas, int64_t* n_lags);
+
+/* Baseline table of a hierarchy (host only, no GPU; bit-exact integers).
+ * dm [n_lags][2 n_levels] int32: the 2n-D lag of every output slot
+ *   (Eq. ProofEq2: each G index runs over -(n-1)..(n-1));
+ * redundancy [n_lags] int64: number of antenna pairs sharing that lag,
+ *   prod_d (n_d - |D_d|) (the baseline distribution d = l * l^- of Sec. III
+ *   for a layout map of ones);
+ * dr [n_lags][2] double: the physical baseline sum_k A_k (D_{2k}, D_{2k+1}).
+ * Any of the three outputs may be NULL.  Returns OMNI_ERR_COLLISION when two
+ * antennas coincide within 1e-9 * max|r|. */
+omni_status omni_baselines(const omni_level* levels, int n_levels, int32_t* dm,
+                           int64_t* redundancy, double* dr);
+
+/* Create a plan on the current CUDA device for C channels of voltages of the
+ * given type.  The plan owns its device accumulator ([C][L] FP64, L =
+ * prod L_d), scratch buffers and staging memory; all are allocated here.
+ * Errors: INVALID_ARG, COLLISION, UNSUPPORTED (more than 8 levels, a padded
+ * axis longer than 4096, or a non-power-of-two padded axis longer than 1024),
+ * OOM, CUDA. */
+omni_status omni_plan_create(const omni_level* levels, int n_levels, int64_t n_channels,
+                             omni_dtype dtype, omni_precision precision, omni_plan** out);
+
+/* Free everything the plan owns (synchronises its device work first). */
+void omni_plan_destroy(omni_plan* plan);
+
+/* Shape of a plan: n_dims = 2 n_levels; dims/padded receive n_d and L_d
+ * ([n_dims] each, may be NULL). */
+omni_status omni_plan_info(const omni_plan* plan, int* n_dims, int32_t* dims,
+                           int32_t* padded, int64_t* n_antennas, int64_t* n_lags,
+                           int64_t* n_channels);
+
+/* Accumulate T samples of every channel (Sec. II.C: FFT, |.|^2, summed over
+ * time; Appendix A steps 3-5).  volts_dev: DEVICE pointer to [C][T][N]
+ * complex voltages of the plan's dtype, 16-byte aligned, owned by the caller
+ * and only read.  T >= 0 (T = 0 is a no-op).  Asynchronous on stream. */
+omni_status omni_correlate(omni_plan* plan, const void* volts_dev, int64_t T, void* stream);
+
+/* Same as omni_correlate for voltages in HOST memory (pageable or pinned):
+ * the plan copies them to the device in chunks, overlapping the copies with
+ * the transforms, and returns once the host buffer may be reused (the
+ * transforms may still be running on stream). */
+omni_status omni_correlate_host(omni_plan* plan, const void* volts_host, int64_t T,
+                                void* stream);
+
+/* Inverse-transform the accumulated |F|^2 into visibilities (Sec. II.C) and
+ * write them to vis_dev, a DEVICE pointer to [C][n_lags] complex128
+ * (interleaved re, im doubles) owned by the caller.  reset != 0 clears the
+ * accumulator afterwards so that the next omni_correlate starts a new
+ * integration.  Synchronises the stream and reports earlier device errors. */
+omni_status omni_visibilities(omni_plan* plan, double* vis_dev, int reset, void* stream);
+
+/* Same as omni_visibilities with vis_host in HOST memory. */
+omni_status omni_visibilities_host(omni_plan* plan, double* vis_host, int reset,
+                                   void* stream);
+
+/* Clear the accumulator (start a new integration) without producing output. */
+omni_status omni_reset(omni_plan* plan, void* stream);
+
+/* Wait for the plan's work on stream and report any device error. */
+omni_status omni_sync(omni_plan* plan, void* stream);
+
+/* Per-kernel statistics of a plan (see omni_profile_*). */
+typedef struct omni_kernel_stat {
+    char name[64];     /* pass name, e.g. "fwd axis3 reg16 last" */
+    int64_t launches;  /* kernel launches of this pass */
+    double total_ms;   /* summed durations from CUDA events recorded around each
+                          launch on the launching stream (0 unless profiling) */
+    double bytes;      /* algorithmic bytes of all launches: inputs read plus
+                          outputs written at their stored precision */
+} omni_kernel_stat;
+
+/* Start (enable != 0) or stop recording a CUDA event pair around every kernel
+ * launch of the plan.  Launch counts are kept whether or not profiling is on. */
+omni_status omni_profile_enable(omni_plan* plan, int enable);
+
+/* Copy up to max per-pass statistics into out (n_out receives how many);
+ * waits for the recorded events.  clear != 0 resets the statistics. */
+omni_status omni_profile_read(omni_plan* plan, omni_kernel_stat* out, int max, int* n_out,
+                              int clear);
+
+/* Message describing the calling thread's most recent failure ("" if none). */
+const char* omni_last_error(void);
+
+/* Static name of a status code. */
+const char* omni_status_string(omni_status status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OMNI_H */

@@ -24,6 +24,9 @@
  * invariants, a naive-DFT route and a numpy.fft route).
  */
 #include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -256,3 +259,13 @@ void oracle_correlate_selected(int D, const int32_t *n, int64_t C, int64_t T, in
 }
 
 int oracle_max_dims(void) { return OR_MAX_DIMS; }
+
+/* Threads the OpenMP loops above use. */
+int oracle_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

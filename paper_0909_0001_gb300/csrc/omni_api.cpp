@@ -1,0 +1,767 @@
+// omni_api.cpp -- host side of the C ABI declared in include/omni.h.
+//
+// Validates hierarchies, builds the lattice geometry (Eq. GridEq) and the
+// baseline tables (Eq. ProofEq2 index ranges, Sec. III redundancy), owns the
+// device accumulator and scratch, and sequences the per-axis passes of the
+// correlator: forward passes over chunks of samples with |F|^2 summed into the
+// FP64 accumulator, then inverse passes that produce the visibilities.
+#include "omni.h"
+#include "omni_internal.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+using namespace omni;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+omni_status fail(omni_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+omni_status cuda_fail(cudaError_t e, const char* what) {
+    return fail(e == cudaErrorMemoryAllocation ? OMNI_ERR_OOM : OMNI_ERR_CUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+#define OMNI_CUDA(call, what)                        \
+    do {                                             \
+        cudaError_t e_ = (call);                     \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+bool is_pow2(int64_t x) { return x > 0 && (x & (x - 1)) == 0; }
+
+// Lattice geometry of a validated hierarchy.
+struct Geometry {
+    int n_levels = 0;
+    int D = 0;
+    int32_t n[kMaxDims] = {};
+    int32_t Lp[kMaxDims] = {};
+    int64_t N = 1, L = 1, Q = 1;
+    std::vector<double> A;  // [n_levels][4]
+};
+
+omni_status make_geometry(const omni_level* levels, int n_levels, Geometry& g) {
+    if (!levels) return fail(OMNI_ERR_INVALID_ARG, "levels is NULL");
+    if (n_levels < 1 || n_levels > kMaxDims / 2)
+        return fail(OMNI_ERR_INVALID_ARG, "n_levels must be in [1, %d], got %d", kMaxDims / 2, n_levels);
+    g.n_levels = n_levels;
+    g.D = 2 * n_levels;
+    g.A.assign(4 * n_levels, 0.0);
+    for (int k = 0; k < n_levels; ++k) {
+        const omni_level& lv = levels[k];
+        if (lv.n1 < 1 || lv.n2 < 1)
+            return fail(OMNI_ERR_INVALID_ARG, "level %d has shape %d x %d; sizes must be >= 1", k + 1,
+                        lv.n1, lv.n2);
+        for (int c = 0; c < 4; ++c) {
+            if (!std::isfinite(lv.A[c])) return fail(OMNI_ERR_INVALID_ARG, "level %d matrix is not finite", k + 1);
+            g.A[4 * k + c] = lv.A[c];
+        }
+        g.n[2 * k] = lv.n1;
+        g.n[2 * k + 1] = lv.n2;
+    }
+    for (int d = 0; d < g.D; ++d) {
+        const int64_t nd = g.n[d];
+        const int64_t Ld = nd > 1 ? 2 * nd : 1;
+        if (g.N > (int64_t(1) << 40) / nd) return fail(OMNI_ERR_UNSUPPORTED, "too many antennas");
+        g.N *= nd;
+        g.L *= Ld;
+        g.Q *= 2 * nd - 1;
+        if (Ld > kTwiddleN) return fail(OMNI_ERR_UNSUPPORTED, "padded axis %d has length %lld > %d", d, (long long)Ld, kTwiddleN);
+        if (!is_pow2(Ld) && Ld > 1024)
+            return fail(OMNI_ERR_UNSUPPORTED, "padded axis %d has non-power-of-two length %lld > 1024", d, (long long)Ld);
+        g.Lp[d] = (int32_t)Ld;
+    }
+    return OMNI_OK;
+}
+
+// Antenna positions r_i = sum_k A_k m_k (Eq. GridEq), antenna order dimension 0 fastest.
+void positions(const Geometry& g, std::vector<double>& r) {
+    r.assign(2 * g.N, 0.0);
+    for (int64_t i = 0; i < g.N; ++i) {
+        int64_t rest = i;
+        double x = 0.0, y = 0.0;
+        for (int k = 0; k < g.n_levels; ++k) {
+            const int64_t m1 = rest % g.n[2 * k];
+            rest /= g.n[2 * k];
+            const int64_t m2 = rest % g.n[2 * k + 1];
+            rest /= g.n[2 * k + 1];
+            const double* a = &g.A[4 * k];
+            x += a[0] * m1 + a[1] * m2;
+            y += a[2] * m1 + a[3] * m2;
+        }
+        r[2 * i] = x;
+        r[2 * i + 1] = y;
+    }
+}
+
+// Sec. II.D requires the map from r to the index set to be unique: reject two
+// antennas closer than 1e-9 max|r| (exactly coincident when max|r| = 0).
+// Spatial hash with cells of the tolerance size; each point checks the 3x3
+// neighbouring cells.
+omni_status check_unique(const Geometry& g) {
+    if (g.N < 2) return OMNI_OK;
+    std::vector<double> r;
+    positions(g, r);
+    double rmax = 0.0;
+    for (int64_t i = 0; i < g.N; ++i) rmax = std::max(rmax, std::hypot(r[2 * i], r[2 * i + 1]));
+    const double tol = 1e-9 * rmax;
+    const double cell = tol > 0.0 ? tol : 1.0;
+    struct Key {
+        int64_t x, y;
+        bool operator==(const Key& o) const { return x == o.x && y == o.y; }
+    };
+    struct KeyHash {
+        size_t operator()(const Key& k) const {
+            return std::hash<int64_t>()(k.x * 0x9E3779B97F4A7C15ULL ^ (uint64_t)k.y);
+        }
+    };
+    std::unordered_map<Key, std::vector<int64_t>, KeyHash> grid;
+    grid.reserve((size_t)g.N * 2);
+    for (int64_t i = 0; i < g.N; ++i) {
+        const Key k{(int64_t)std::floor(r[2 * i] / cell), (int64_t)std::floor(r[2 * i + 1] / cell)};
+        for (int64_t dx = -1; dx <= 1; ++dx)
+            for (int64_t dy = -1; dy <= 1; ++dy) {
+                auto it = grid.find(Key{k.x + dx, k.y + dy});
+                if (it == grid.end()) continue;
+                for (int64_t j : it->second)
+                    if (std::hypot(r[2 * i] - r[2 * j], r[2 * i + 1] - r[2 * j + 1]) <= tol)
+                        return fail(OMNI_ERR_COLLISION,
+                                    "antennas %lld and %lld coincide at (%g, %g): the hierarchy "
+                                    "does not map positions to unique indices",
+                                    (long long)j, (long long)i, r[2 * i], r[2 * i + 1]);
+            }
+        grid[k].push_back(i);
+    }
+    return OMNI_OK;
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------------------- plan
+
+struct omni_plan {
+    int device = 0;
+    Geometry g;
+    int64_t C = 0;
+    omni_dtype dtype = OMNI_IN_CF32;
+    omni_precision precision = OMNI_FP32;
+    std::vector<Pass> fwd, inv;
+    int64_t Cc = 1, Tc = 1;   // forward chunk: channels x samples
+    int64_t Cv = 1;           // inverse batch: channels
+    int64_t fwd_elems = 0;    // float2 per sample, largest non-final forward output
+    int64_t inv_elems = 0;    // float2 per channel, largest non-final inverse output
+    float2* buf[2] = {nullptr, nullptr};
+    int64_t buf_elems = 0;
+    double* P = nullptr;      // [C][L]
+    std::vector<float2*> tw_tables;
+    // host-input staging
+    void* stage[2] = {nullptr, nullptr};
+    size_t stage_bytes = 0;
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ready[2] = {nullptr, nullptr};
+    cudaEvent_t freed[2] = {nullptr, nullptr};
+    double2* vis_tmp = nullptr;  // device staging for omni_visibilities_host
+    // statistics per pass: forward passes first, then inverse passes
+    std::vector<omni_kernel_stat> stats;
+    bool profiling = false;
+    struct Pending {
+        int pass;
+        cudaEvent_t start, stop;
+    };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> event_pool;
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+int elem_bytes(omni_dtype t) { return t == OMNI_IN_CI8 ? 2 : 8; }
+
+void choose_kind(Pass& p) {
+    if (p.L == 1) {
+        p.kind = KIND_DIRECT;
+    } else if (is_pow2(p.L) && p.L <= 64) {
+        p.kind = KIND_REG;
+    } else if (is_pow2(p.L) && p.L <= kTwiddleN) {
+        p.kind = KIND_SMEM;
+        switch (p.L) {
+            case 128: p.L1 = 16; p.L2 = 8; break;
+            case 256: p.L1 = 16; p.L2 = 16; break;
+            case 512: p.L1 = 32; p.L2 = 16; break;
+            case 1024: p.L1 = 32; p.L2 = 32; break;
+            case 2048: p.L1 = 64; p.L2 = 32; break;
+            default: p.L1 = 64; p.L2 = 64; break;
+        }
+        int W = 256 / p.L1;
+        while (W > 1 && W / 2 >= p.inner) W /= 2;
+        p.W = W;
+    } else {
+        p.kind = KIND_DIRECT;
+    }
+}
+
+omni_status build_passes(omni_plan* pl) {
+    const Geometry& g = pl->g;
+    std::vector<int> axes;
+    for (int d = 0; d < g.D; ++d)
+        if (g.Lp[d] > 1) axes.push_back(d);
+    if (axes.empty()) axes.push_back(0);  // a single antenna: an identity "transform"
+    // forward: increasing axis order; inputs [outer n_e>d][n_d][inner L_e<d]
+    pl->fwd.clear();
+    pl->fwd_elems = 0;
+    for (size_t a = 0; a < axes.size(); ++a) {
+        const int d = axes[a];
+        Pass p{};
+        p.axis = d;
+        p.L = g.Lp[d];
+        p.n = g.n[d];
+        p.q_out = g.Lp[d];
+        p.inner = 1;
+        p.outer = 1;
+        for (int e = 0; e < d; ++e) p.inner *= g.Lp[e];
+        for (int e = d + 1; e < g.D; ++e) p.outer *= g.n[e];
+        p.mode = (a + 1 == axes.size()) ? MODE_LAST : MODE_MID;
+        choose_kind(p);
+        if (p.mode == MODE_MID) pl->fwd_elems = std::max(pl->fwd_elems, p.outer * p.L * p.inner);
+        pl->fwd.push_back(p);
+    }
+    // inverse: decreasing axis order; inputs [outer Q_e>d][L_d][inner L_e<d]
+    pl->inv.clear();
+    pl->inv_elems = 0;
+    for (size_t a = axes.size(); a-- > 0;) {
+        const int d = axes[a];
+        Pass p{};
+        p.axis = d;
+        p.L = g.Lp[d];
+        p.n = g.Lp[d];
+        p.q_out = 2 * g.n[d] - 1;
+        p.q_shift = g.n[d] - 1;
+        p.inner = 1;
+        p.outer = 1;
+        for (int e = 0; e < d; ++e) p.inner *= g.Lp[e];
+        for (int e = d + 1; e < g.D; ++e) p.outer *= 2 * g.n[e] - 1;
+        p.mode = (a == 0) ? MODE_INV_LAST : MODE_INV_MID;
+        choose_kind(p);
+        if (p.mode == MODE_INV_MID) pl->inv_elems = std::max(pl->inv_elems, p.outer * p.q_out * p.inner);
+        pl->inv.push_back(p);
+    }
+    // direct-DFT twiddle tables w_L^m, m < L, computed in double
+    for (auto* list : {&pl->fwd, &pl->inv})
+        for (Pass& p : *list) {
+            if (p.kind != KIND_DIRECT) continue;
+            std::vector<float2> h(p.L);
+            for (int m = 0; m < p.L; ++m) {
+                const double ang = 6.283185307179586476925286766559 * m / p.L;
+                h[m] = make_float2((float)std::cos(ang), (float)-std::sin(ang));
+            }
+            float2* dptr = nullptr;
+            OMNI_CUDA(cudaMalloc(&dptr, sizeof(float2) * p.L), "cudaMalloc(twiddles)");
+            pl->tw_tables.push_back(dptr);
+            OMNI_CUDA(cudaMemcpy(dptr, h.data(), sizeof(float2) * p.L, cudaMemcpyHostToDevice),
+                      "cudaMemcpy(twiddles)");
+            p.tw = dptr;
+        }
+    return OMNI_OK;
+}
+
+// Chunk sizes: each scratch buffer holds about OMNI_CHUNK_MB (default 48) MB
+// so a chunk's intermediates stay in L2, and the last pass gets at least ~64K
+// lines of parallel work.
+void choose_chunks(omni_plan* pl) {
+    int64_t mb = 48;
+    if (const char* env = std::getenv("OMNI_CHUNK_MB")) mb = std::max<int64_t>(1, std::atoll(env));
+    const int64_t target = mb << 20;
+    const Pass& last = pl->fwd.back();
+    const int64_t last_lines = std::max<int64_t>(1, last.inner);
+    pl->Cc = std::min<int64_t>(pl->C, std::max<int64_t>(1, (65536 + last_lines - 1) / last_lines));
+    const int64_t per_sample = std::max<int64_t>(1, pl->fwd_elems) * (int64_t)sizeof(float2);
+    const int64_t samples = std::max<int64_t>(1, target / per_sample);
+    pl->Tc = std::max<int64_t>(1, std::min<int64_t>(1024, samples / pl->Cc));
+    const int64_t per_chan = std::max<int64_t>(1, pl->inv_elems) * (int64_t)sizeof(float2);
+    pl->Cv = std::min<int64_t>(pl->C, std::max<int64_t>(1, target / per_chan));
+    pl->buf_elems = std::max(pl->Cc * pl->Tc * pl->fwd_elems, pl->Cv * pl->inv_elems);
+}
+
+void release(omni_plan* pl) {
+    DeviceGuard dg(pl->device);
+    if (pl->copy_stream) cudaStreamSynchronize(pl->copy_stream);
+    cudaFree(pl->buf[0]);
+    cudaFree(pl->buf[1]);
+    cudaFree(pl->P);
+    cudaFree(pl->vis_tmp);
+    for (float2* t : pl->tw_tables) cudaFree(t);
+    for (int b = 0; b < 2; ++b) {
+        cudaFree(pl->stage[b]);
+        if (pl->ready[b]) cudaEventDestroy(pl->ready[b]);
+        if (pl->freed[b]) cudaEventDestroy(pl->freed[b]);
+    }
+    if (pl->copy_stream) cudaStreamDestroy(pl->copy_stream);
+    for (auto& q : pl->pending) {
+        cudaEventDestroy(q.start);
+        cudaEventDestroy(q.stop);
+    }
+    for (cudaEvent_t e : pl->event_pool) cudaEventDestroy(e);
+    delete pl;
+}
+
+const char* kind_name(int k) { return k == KIND_REG ? "reg" : k == KIND_SMEM ? "smem" : "direct"; }
+const char* mode_name(int m) {
+    return m == MODE_MID ? "mid" : m == MODE_LAST ? "last" : m == MODE_INV_MID ? "mid" : "last";
+}
+
+void init_stats(omni_plan* pl) {
+    pl->stats.clear();
+    for (int inv = 0; inv < 2; ++inv)
+        for (const Pass& p : inv ? pl->inv : pl->fwd) {
+            omni_kernel_stat st{};
+            snprintf(st.name, sizeof st.name, "%s axis%d %s%d %s", inv ? "inv" : "fwd", p.axis,
+                     kind_name(p.kind), p.L, mode_name(p.mode));
+            pl->stats.push_back(st);
+        }
+}
+
+cudaEvent_t pool_event(omni_plan* pl) {
+    if (!pl->event_pool.empty()) {
+        cudaEvent_t e = pl->event_pool.back();
+        pl->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// Input element size of a pass source, bytes.
+double src_bytes(int src_kind) {
+    return src_kind == SRC_CI8 ? 2.0 : src_kind == SRC_P64 ? 8.0 : 8.0;
+}
+
+// Algorithmic bytes of one launch: inputs read plus outputs written.
+double pass_bytes(const Pass& p, const PassArgs& a) {
+    const double in = src_bytes(a.src_kind);
+    switch (p.mode) {
+        case MODE_MID:
+            return (double)a.S * p.outer * p.inner * (p.n * in + p.L * 8.0);
+        case MODE_LAST:
+            return (double)a.S * a.tc * p.inner * p.n * in + (double)a.S * p.L * p.inner * 16.0;
+        case MODE_INV_MID:
+            return (double)a.S * p.outer * p.inner * (p.n * in + p.q_out * 8.0);
+        default:
+            return (double)a.S * p.outer * p.inner * (p.n * in + p.q_out * 16.0);
+    }
+}
+
+// Launch pass number idx (index into stats) with optional event timing.
+cudaError_t launch_counted(omni_plan* pl, int idx, const Pass& p, const PassArgs& a,
+                           cudaStream_t st) {
+    omni_kernel_stat& s = pl->stats[idx];
+    s.launches += 1;
+    s.bytes += pass_bytes(p, a);
+    if (!pl->profiling) return launch_pass(p, a, st);
+    cudaEvent_t e0 = pool_event(pl), e1 = pool_event(pl);
+    if (!e0 || !e1) return cudaErrorMemoryAllocation;
+    cudaEventRecord(e0, st);
+    cudaError_t e = launch_pass(p, a, st);
+    cudaEventRecord(e1, st);
+    pl->pending.push_back({idx, e0, e1});
+    return e;
+}
+
+// One chunk of forward passes: channels [c0, c0+cc) x samples [t0, t0+tc).
+omni_status run_chunk(omni_plan* pl, const void* volts, int64_t vc0, int64_t Tsrc, int64_t t0,
+                      int64_t c0, int64_t cc, int64_t tc, cudaStream_t st) {
+    const void* src = volts;
+    int src_kind = pl->dtype == OMNI_IN_CI8 ? SRC_CI8 : SRC_CF32;
+    int64_t src_stride = 0;
+    for (size_t k = 0; k < pl->fwd.size(); ++k) {
+        const Pass& p = pl->fwd[k];
+        PassArgs a{};
+        a.src = src;
+        a.src_kind = src_kind;
+        a.src_stride = src_stride;
+        a.vc0 = vc0;
+        a.T = Tsrc;
+        a.t0 = t0;
+        a.N = pl->g.N;
+        a.tc = (int)tc;
+        a.c0 = c0;
+        a.P = pl->P;
+        a.P_stride = pl->g.L;
+        float2* dst = pl->buf[k & 1];
+        if (p.mode == MODE_LAST) {
+            a.S = cc;
+        } else {
+            a.S = cc * tc;
+            a.dst = dst;
+            a.dst_stride = p.outer * p.L * p.inner;
+        }
+        cudaError_t e = launch_counted(pl, (int)k, p, a, st);
+        if (e != cudaSuccess) return cuda_fail(e, "forward pass launch");
+        src = dst;
+        src_kind = SRC_BUF;
+        src_stride = p.outer * p.L * p.inner;
+    }
+    return OMNI_OK;
+}
+
+omni_status check_plan(omni_plan* pl) {
+    if (!pl) return fail(OMNI_ERR_INVALID_ARG, "plan is NULL");
+    return OMNI_OK;
+}
+
+omni_status run_inverse(omni_plan* pl, double2* V, cudaStream_t st) {
+    for (int64_t c0 = 0; c0 < pl->C; c0 += pl->Cv) {
+        const int64_t cv = std::min(pl->Cv, pl->C - c0);
+        const void* src = pl->P;
+        int src_kind = SRC_P64;
+        int64_t src_stride = pl->g.L;
+        for (size_t k = 0; k < pl->inv.size(); ++k) {
+            const Pass& p = pl->inv[k];
+            PassArgs a{};
+            a.src = src;
+            a.src_kind = src_kind;
+            a.src_stride = src_stride;
+            a.S = cv;
+            a.c0 = c0;
+            a.tc = 1;
+            float2* dst = pl->buf[k & 1];
+            if (p.mode == MODE_INV_LAST) {
+                a.V = V;
+                a.V_stride = pl->g.Q;
+                a.scale = 1.0 / (double)pl->g.L;
+            } else {
+                a.dst = dst;
+                a.dst_stride = p.outer * p.q_out * p.inner;
+            }
+            cudaError_t e = launch_counted(pl, (int)(pl->fwd.size() + k), p, a, st);
+            if (e != cudaSuccess) return cuda_fail(e, "inverse pass launch");
+            // later passes read the scratch buffer, indexed from 0 per channel of the
+            // batch (c0 only offsets P and V)
+            src = dst;
+            src_kind = SRC_BUF;
+            src_stride = p.outer * p.q_out * p.inner;
+        }
+    }
+    return OMNI_OK;
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------------------- C ABI
+
+extern "C" {
+
+omni_status omni_lattice_shape(const omni_level* levels, int n_levels, int64_t* n_antennas,
+                               int64_t* n_lags) {
+    Geometry g;
+    omni_status st = make_geometry(levels, n_levels, g);
+    if (st != OMNI_OK) return st;
+    if (n_antennas) *n_antennas = g.N;
+    if (n_lags) *n_lags = g.Q;
+    return OMNI_OK;
+}
+
+omni_status omni_baselines(const omni_level* levels, int n_levels, int32_t* dm, int64_t* redundancy,
+                           double* dr) {
+    Geometry g;
+    omni_status st = make_geometry(levels, n_levels, g);
+    if (st != OMNI_OK) return st;
+    st = check_unique(g);
+    if (st != OMNI_OK) return st;
+    int32_t lag[kMaxDims];
+    for (int d = 0; d < g.D; ++d) lag[d] = -(g.n[d] - 1);
+    for (int64_t q = 0; q < g.Q; ++q) {
+        int64_t red = 1;
+        double x = 0.0, y = 0.0;
+        for (int d = 0; d < g.D; ++d) {
+            if (dm) dm[q * g.D + d] = lag[d];
+            red *= g.n[d] - std::abs(lag[d]);
+        }
+        for (int k = 0; k < g.n_levels; ++k) {
+            const double* a = &g.A[4 * k];
+            x += a[0] * lag[2 * k] + a[1] * lag[2 * k + 1];
+            y += a[2] * lag[2 * k] + a[3] * lag[2 * k + 1];
+        }
+        if (redundancy) redundancy[q] = red;
+        if (dr) {
+            dr[2 * q] = x;
+            dr[2 * q + 1] = y;
+        }
+        for (int d = 0; d < g.D; ++d) {  // odometer, dimension 0 fastest
+            if (++lag[d] <= g.n[d] - 1) break;
+            lag[d] = -(g.n[d] - 1);
+        }
+    }
+    return OMNI_OK;
+}
+
+omni_status omni_plan_create(const omni_level* levels, int n_levels, int64_t n_channels,
+                             omni_dtype dtype, omni_precision precision, omni_plan** out) {
+    if (!out) return fail(OMNI_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n_channels < 1) return fail(OMNI_ERR_INVALID_ARG, "n_channels must be >= 1");
+    if (dtype != OMNI_IN_CF32 && dtype != OMNI_IN_CI8) return fail(OMNI_ERR_INVALID_ARG, "unknown dtype %d", (int)dtype);
+    if (precision != OMNI_FP32 && precision != OMNI_MIXED_FP16)
+        return fail(OMNI_ERR_INVALID_ARG, "unknown precision %d", (int)precision);
+    omni_plan* pl = new omni_plan();
+    omni_status st = make_geometry(levels, n_levels, pl->g);
+    if (st == OMNI_OK) st = check_unique(pl->g);
+    if (st != OMNI_OK) {
+        delete pl;
+        return st;
+    }
+    if (precision == OMNI_MIXED_FP16) {
+        delete pl;
+        return fail(OMNI_ERR_UNSUPPORTED, "the mixed-precision path is not available for this hierarchy");
+    }
+    pl->C = n_channels;
+    pl->dtype = dtype;
+    pl->precision = precision;
+    cudaError_t e = cudaGetDevice(&pl->device);
+    if (e != cudaSuccess) {
+        delete pl;
+        return cuda_fail(e, "cudaGetDevice");
+    }
+    e = init_device_tables();
+    if (e != cudaSuccess) {
+        delete pl;
+        return cuda_fail(e, "twiddle table upload");
+    }
+    st = build_passes(pl);
+    if (st != OMNI_OK) {
+        release(pl);
+        return st;
+    }
+    choose_chunks(pl);
+    init_stats(pl);
+    const size_t buf_bytes = (size_t)std::max<int64_t>(1, pl->buf_elems) * sizeof(float2);
+    const size_t P_bytes = (size_t)pl->C * pl->g.L * sizeof(double);
+    if ((e = cudaMalloc(&pl->buf[0], buf_bytes)) != cudaSuccess ||
+        (e = cudaMalloc(&pl->buf[1], buf_bytes)) != cudaSuccess ||
+        (e = cudaMalloc(&pl->P, P_bytes)) != cudaSuccess ||
+        (e = cudaMemset(pl->P, 0, P_bytes)) != cudaSuccess) {
+        release(pl);
+        return cuda_fail(e, "allocating plan buffers");
+    }
+    *out = pl;
+    return OMNI_OK;
+}
+
+void omni_plan_destroy(omni_plan* plan) {
+    if (plan) release(plan);
+}
+
+omni_status omni_plan_info(const omni_plan* pl, int* n_dims, int32_t* dims, int32_t* padded,
+                           int64_t* n_antennas, int64_t* n_lags, int64_t* n_channels) {
+    if (!pl) return fail(OMNI_ERR_INVALID_ARG, "plan is NULL");
+    if (n_dims) *n_dims = pl->g.D;
+    for (int d = 0; d < pl->g.D; ++d) {
+        if (dims) dims[d] = pl->g.n[d];
+        if (padded) padded[d] = pl->g.Lp[d];
+    }
+    if (n_antennas) *n_antennas = pl->g.N;
+    if (n_lags) *n_lags = pl->g.Q;
+    if (n_channels) *n_channels = pl->C;
+    return OMNI_OK;
+}
+
+omni_status omni_correlate(omni_plan* pl, const void* volts_dev, int64_t T, void* stream) {
+    omni_status st = check_plan(pl);
+    if (st != OMNI_OK) return st;
+    if (T < 0) return fail(OMNI_ERR_INVALID_ARG, "T must be >= 0");
+    if (T == 0) return OMNI_OK;
+    if (!volts_dev) return fail(OMNI_ERR_INVALID_ARG, "volts_dev is NULL");
+    if ((uintptr_t)volts_dev % 16 != 0) return fail(OMNI_ERR_INVALID_ARG, "volts_dev must be 16-byte aligned");
+    DeviceGuard dg(pl->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int64_t c0 = 0; c0 < pl->C; c0 += pl->Cc) {
+        const int64_t cc = std::min(pl->Cc, pl->C - c0);
+        for (int64_t t0 = 0; t0 < T; t0 += pl->Tc) {
+            const int64_t tc = std::min(pl->Tc, T - t0);
+            st = run_chunk(pl, volts_dev, c0, T, t0, c0, cc, tc, s);
+            if (st != OMNI_OK) return st;
+        }
+    }
+    return OMNI_OK;
+}
+
+omni_status omni_correlate_host(omni_plan* pl, const void* volts_host, int64_t T, void* stream) {
+    omni_status st = check_plan(pl);
+    if (st != OMNI_OK) return st;
+    if (T < 0) return fail(OMNI_ERR_INVALID_ARG, "T must be >= 0");
+    if (T == 0) return OMNI_OK;
+    if (!volts_host) return fail(OMNI_ERR_INVALID_ARG, "volts_host is NULL");
+    DeviceGuard dg(pl->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t eb = (size_t)elem_bytes(pl->dtype);
+    const size_t row = (size_t)pl->g.N * eb;  // one sample of one channel
+    const size_t need = (size_t)pl->Cc * pl->Tc * row;
+    if (pl->stage_bytes < need) {
+        OMNI_CUDA(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+        for (int b = 0; b < 2; ++b) {
+            cudaFree(pl->stage[b]);
+            pl->stage[b] = nullptr;
+        }
+        pl->stage_bytes = 0;
+        for (int b = 0; b < 2; ++b) OMNI_CUDA(cudaMalloc(&pl->stage[b], need), "cudaMalloc(staging)");
+        pl->stage_bytes = need;
+    }
+    if (!pl->copy_stream) {
+        OMNI_CUDA(cudaStreamCreateWithFlags(&pl->copy_stream, cudaStreamNonBlocking), "cudaStreamCreate");
+        for (int b = 0; b < 2; ++b) {
+            OMNI_CUDA(cudaEventCreateWithFlags(&pl->ready[b], cudaEventDisableTiming), "cudaEventCreate");
+            OMNI_CUDA(cudaEventCreateWithFlags(&pl->freed[b], cudaEventDisableTiming), "cudaEventCreate");
+        }
+    }
+    // copies of chunk j must wait for the compute stream to have consumed the
+    // staging buffer of chunk j-2 ('freed'); compute waits for 'ready'.
+    OMNI_CUDA(cudaEventRecord(pl->freed[0], s), "cudaEventRecord");
+    OMNI_CUDA(cudaEventRecord(pl->freed[1], s), "cudaEventRecord");
+    int64_t j = 0;
+    for (int64_t c0 = 0; c0 < pl->C; c0 += pl->Cc) {
+        const int64_t cc = std::min(pl->Cc, pl->C - c0);
+        for (int64_t t0 = 0; t0 < T; t0 += pl->Tc, ++j) {
+            const int64_t tc = std::min(pl->Tc, T - t0);
+            const int b = (int)(j & 1);
+            OMNI_CUDA(cudaStreamWaitEvent(pl->copy_stream, pl->freed[b], 0), "cudaStreamWaitEvent");
+            for (int64_t k = 0; k < cc; ++k) {
+                const char* hsrc = (const char*)volts_host + ((size_t)(c0 + k) * T + t0) * row;
+                char* ddst = (char*)pl->stage[b] + (size_t)k * tc * row;
+                OMNI_CUDA(cudaMemcpyAsync(ddst, hsrc, (size_t)tc * row, cudaMemcpyHostToDevice, pl->copy_stream),
+                          "cudaMemcpyAsync(H2D)");
+            }
+            OMNI_CUDA(cudaEventRecord(pl->ready[b], pl->copy_stream), "cudaEventRecord");
+            OMNI_CUDA(cudaStreamWaitEvent(s, pl->ready[b], 0), "cudaStreamWaitEvent");
+            st = run_chunk(pl, pl->stage[b], 0, tc, 0, c0, cc, tc, s);
+            if (st != OMNI_OK) return st;
+            OMNI_CUDA(cudaEventRecord(pl->freed[b], s), "cudaEventRecord");
+        }
+    }
+    OMNI_CUDA(cudaStreamSynchronize(pl->copy_stream), "cudaStreamSynchronize(copy)");
+    return OMNI_OK;
+}
+
+omni_status omni_visibilities(omni_plan* pl, double* vis_dev, int reset, void* stream) {
+    omni_status st = check_plan(pl);
+    if (st != OMNI_OK) return st;
+    if (!vis_dev) return fail(OMNI_ERR_INVALID_ARG, "vis_dev is NULL");
+    if ((uintptr_t)vis_dev % 16 != 0) return fail(OMNI_ERR_INVALID_ARG, "vis_dev must be 16-byte aligned");
+    DeviceGuard dg(pl->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    st = run_inverse(pl, reinterpret_cast<double2*>(vis_dev), s);
+    if (st != OMNI_OK) return st;
+    if (reset) OMNI_CUDA(cudaMemsetAsync(pl->P, 0, (size_t)pl->C * pl->g.L * sizeof(double), s), "cudaMemsetAsync");
+    OMNI_CUDA(cudaStreamSynchronize(s), "device error during correlation");
+    return OMNI_OK;
+}
+
+omni_status omni_visibilities_host(omni_plan* pl, double* vis_host, int reset, void* stream) {
+    omni_status st = check_plan(pl);
+    if (st != OMNI_OK) return st;
+    if (!vis_host) return fail(OMNI_ERR_INVALID_ARG, "vis_host is NULL");
+    DeviceGuard dg(pl->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t bytes = (size_t)pl->C * pl->g.Q * sizeof(double2);
+    if (!pl->vis_tmp) OMNI_CUDA(cudaMalloc(&pl->vis_tmp, bytes), "cudaMalloc(visibility staging)");
+    st = run_inverse(pl, pl->vis_tmp, s);
+    if (st != OMNI_OK) return st;
+    if (reset) OMNI_CUDA(cudaMemsetAsync(pl->P, 0, (size_t)pl->C * pl->g.L * sizeof(double), s), "cudaMemsetAsync");
+    OMNI_CUDA(cudaMemcpyAsync(vis_host, pl->vis_tmp, bytes, cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync(D2H)");
+    OMNI_CUDA(cudaStreamSynchronize(s), "device error during correlation");
+    return OMNI_OK;
+}
+
+omni_status omni_reset(omni_plan* pl, void* stream) {
+    omni_status st = check_plan(pl);
+    if (st != OMNI_OK) return st;
+    DeviceGuard dg(pl->device);
+    OMNI_CUDA(cudaMemsetAsync(pl->P, 0, (size_t)pl->C * pl->g.L * sizeof(double), (cudaStream_t)stream),
+              "cudaMemsetAsync");
+    return OMNI_OK;
+}
+
+omni_status omni_sync(omni_plan* pl, void* stream) {
+    omni_status st = check_plan(pl);
+    if (st != OMNI_OK) return st;
+    DeviceGuard dg(pl->device);
+    OMNI_CUDA(cudaStreamSynchronize((cudaStream_t)stream), "device error");
+    return OMNI_OK;
+}
+
+omni_status omni_profile_enable(omni_plan* pl, int enable) {
+    omni_status st = check_plan(pl);
+    if (st != OMNI_OK) return st;
+    pl->profiling = enable != 0;
+    return OMNI_OK;
+}
+
+omni_status omni_profile_read(omni_plan* pl, omni_kernel_stat* out, int max, int* n_out, int clear) {
+    omni_status st = check_plan(pl);
+    if (st != OMNI_OK) return st;
+    DeviceGuard dg(pl->device);
+    for (auto& q : pl->pending) {
+        OMNI_CUDA(cudaEventSynchronize(q.stop), "cudaEventSynchronize");
+        float ms = 0.f;
+        OMNI_CUDA(cudaEventElapsedTime(&ms, q.start, q.stop), "cudaEventElapsedTime");
+        pl->stats[q.pass].total_ms += ms;
+        pl->event_pool.push_back(q.start);
+        pl->event_pool.push_back(q.stop);
+    }
+    pl->pending.clear();
+    const int n = (int)std::min<size_t>(pl->stats.size(), max > 0 ? (size_t)max : 0);
+    if (out)
+        for (int i = 0; i < n; ++i) out[i] = pl->stats[i];
+    if (n_out) *n_out = (int)pl->stats.size();
+    if (clear)
+        for (auto& s : pl->stats) {
+            s.launches = 0;
+            s.total_ms = 0.0;
+            s.bytes = 0.0;
+        }
+    return OMNI_OK;
+}
+
+const char* omni_last_error(void) { return g_last_error.c_str(); }
+
+const char* omni_status_string(omni_status s) {
+    switch (s) {
+        case OMNI_OK: return "OMNI_OK";
+        case OMNI_ERR_INVALID_ARG: return "OMNI_ERR_INVALID_ARG";
+        case OMNI_ERR_COLLISION: return "OMNI_ERR_COLLISION";
+        case OMNI_ERR_UNSUPPORTED: return "OMNI_ERR_UNSUPPORTED";
+        case OMNI_ERR_OOM: return "OMNI_ERR_OOM";
+        case OMNI_ERR_CUDA: return "OMNI_ERR_CUDA";
+        case OMNI_ERR_TIMEOUT: return "OMNI_ERR_TIMEOUT";
+    }
+    return "OMNI_ERR_UNKNOWN";
+}
+
+}  // extern "C"

@@ -1,0 +1,48 @@
+// omni_dispatch.cpp -- routes a pass to its kernel family and sets up the
+// per-device twiddle tables of every kernel translation unit.
+#include "omni_internal.h"
+
+#include <mutex>
+#include <vector>
+
+namespace omni {
+
+cudaError_t launch_reg_a(const Pass& p, const PassArgs& a, cudaStream_t st);
+cudaError_t launch_reg_b(const Pass& p, const PassArgs& a, cudaStream_t st);
+cudaError_t launch_smem_a(const Pass& p, const PassArgs& a, cudaStream_t st);
+cudaError_t launch_smem_b(const Pass& p, const PassArgs& a, cudaStream_t st);
+cudaError_t launch_smem_c(const Pass& p, const PassArgs& a, cudaStream_t st);
+cudaError_t launch_direct(const Pass& p, const PassArgs& a, cudaStream_t st);
+cudaError_t upload_twiddles_reg_a();
+cudaError_t upload_twiddles_reg_b();
+cudaError_t upload_twiddles_smem_a();
+cudaError_t upload_twiddles_smem_b();
+cudaError_t upload_twiddles_smem_c();
+
+cudaError_t launch_pass(const Pass& p, const PassArgs& a, cudaStream_t st) {
+    switch (p.kind) {
+        case KIND_REG: return p.L <= 16 ? launch_reg_a(p, a, st) : launch_reg_b(p, a, st);
+        case KIND_SMEM:
+            return p.L <= 512 ? launch_smem_a(p, a, st)
+                 : p.L <= 2048 ? launch_smem_b(p, a, st) : launch_smem_c(p, a, st);
+        default: return launch_direct(p, a, st);
+    }
+}
+
+cudaError_t init_device_tables() {
+    static std::mutex mu;
+    static std::vector<int> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    for (int d : done)
+        if (d == dev) return cudaSuccess;
+    for (auto up : {upload_twiddles_reg_a, upload_twiddles_reg_b, upload_twiddles_smem_a,
+                    upload_twiddles_smem_b, upload_twiddles_smem_c})
+        if ((e = up()) != cudaSuccess) return e;
+    done.push_back(dev);
+    return cudaSuccess;
+}
+
+}  // namespace omni

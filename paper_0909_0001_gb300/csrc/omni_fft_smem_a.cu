@@ -1,0 +1,17 @@
+// omni_fft_smem_a.cu -- four-step passes of 128, 256 and 512 points.
+#include "omni_fft_smem.cuh"
+
+namespace omni {
+
+cudaError_t launch_smem_a(const Pass& p, const PassArgs& a, cudaStream_t st) {
+    switch (p.L) {
+        case 128: return launch_smem_len<16, 8>(p, a, st);
+        case 256: return launch_smem_len<16, 16>(p, a, st);
+        case 512: return launch_smem_len<32, 16>(p, a, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t upload_twiddles_smem_a() { return upload_twiddles(); }
+
+}  // namespace omni

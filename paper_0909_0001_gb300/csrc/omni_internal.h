@@ -1,0 +1,77 @@
+// omni_internal.h -- types shared by the host orchestration and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace omni {
+
+constexpr int kMaxDims = 16;
+constexpr int kTwiddleN = 4096;  // longest padded axis handled by an FFT pass
+
+// Where a pass reads its lines from.
+enum SrcKind : int {
+    SRC_BUF = 0,   // float2 scratch buffer written by the previous pass
+    SRC_CF32 = 1,  // caller voltages, complex float32 [.][T][N]
+    SRC_CI8 = 2,   // caller voltages, complex int8   [.][T][N]
+    SRC_P64 = 3    // FP64 |F|^2 accumulator [C][L] (real), inverse passes
+};
+
+// What a pass does with the transformed lines.
+enum PassMode : int {
+    MODE_MID = 0,      // forward: write the float2 buffer
+    MODE_LAST = 1,     // forward: |F|^2 summed over the chunk's samples, folded into FP64
+    MODE_INV_MID = 2,  // inverse: gather the kept lags into the float2 buffer
+    MODE_INV_LAST = 3  // inverse: gather, conjugate, scale by 1/L, write complex128
+};
+
+// How a pass transforms one line.
+enum PassKind : int {
+    KIND_REG = 0,    // whole line in one thread's registers (power of two <= 64)
+    KIND_SMEM = 1,   // four-step L = L1 * L2 through shared memory (power of two <= 4096)
+    KIND_DIRECT = 2  // direct DFT from a twiddle table (any length)
+};
+
+// One axis transform.  The data of one sample (or channel) is viewed as
+// [outer][len][inner] with the transformed axis in the middle: inputs
+// [outer][n][inner], outputs [outer][q_out][inner].
+struct Pass {
+    int axis;
+    int kind;
+    int mode;
+    int L;          // transform length (padded axis length)
+    int n;          // inputs per line (n_d forward, L_d inverse)
+    int q_out;      // outputs kept per line (L_d forward, 2 n_d - 1 inverse)
+    int q_shift;    // inverse: output q holds lag q - q_shift, i.e. bin (q - q_shift) mod L
+    int L1, L2;     // KIND_SMEM split
+    int W;          // KIND_SMEM: lines per CTA
+    int64_t inner, outer;
+    const float2* tw;  // KIND_DIRECT: w_L^m = exp(-2 pi i m / L), m < L
+};
+
+// Launch-time arguments of one pass.
+struct PassArgs {
+    const void* src;
+    int src_kind;
+    int64_t src_stride;  // SRC_BUF/SRC_P64: elements per sample (or channel)
+    int64_t vc0;         // voltages: first channel row of the chunk in src
+    int64_t T, t0, N;    // voltages: samples per channel row, first sample, antennas
+    int tc;              // samples per channel in this chunk
+    int64_t S;           // MID/INV: samples (channels) in the launch; LAST: channels
+    int64_t c0;          // channel of the first sample in P / V
+    float2* dst;
+    int64_t dst_stride;  // elements per sample of dst
+    double* P;           // LAST / SRC_P64: accumulator
+    int64_t P_stride;    // elements per channel of P (= L)
+    double2* V;          // INV_LAST output
+    int64_t V_stride;    // lags per channel
+    double scale;        // INV_LAST: 1/L
+};
+
+// Upload the twiddle tables to the current device (once per device).
+cudaError_t init_device_tables();
+
+// Launch one pass on stream.
+cudaError_t launch_pass(const Pass& p, const PassArgs& a, cudaStream_t stream);
+
+}  // namespace omni

@@ -1,0 +1,251 @@
+"""Python binding of the C ABI in include/omni.h (argument marshalling only).
+
+Every step of the correlator runs in the CUDA library
+paper_0909_0001_gb300/lib/libomni.so; this module only converts torch tensors
+and numpy arrays to pointers and sizes.  There is no CPU fallback: if the
+library is missing, loading fails with an error.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence, Tuple
+
+import numpy as np
+import torch
+
+from .synth import Level
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "lib", "libomni.so")
+
+OMNI_OK = 0
+STATUS_NAMES = {0: "OMNI_OK", 1: "OMNI_ERR_INVALID_ARG", 2: "OMNI_ERR_COLLISION",
+                3: "OMNI_ERR_UNSUPPORTED", 4: "OMNI_ERR_OOM", 5: "OMNI_ERR_CUDA",
+                6: "OMNI_ERR_TIMEOUT"}
+DTYPES = {"cf32": 0, "ci8": 1}
+PRECISIONS = {"fp32": 0, "mixed": 1}
+
+# every entry point include/omni.h declares
+EXPORTS = (
+    "omni_lattice_shape", "omni_baselines", "omni_plan_create", "omni_plan_destroy",
+    "omni_plan_info", "omni_correlate", "omni_correlate_host", "omni_visibilities",
+    "omni_visibilities_host", "omni_reset", "omni_sync", "omni_last_error",
+    "omni_status_string", "omni_profile_enable", "omni_profile_read",
+)
+
+
+class OmniError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class omni_level(ctypes.Structure):
+    _fields_ = [("n1", ctypes.c_int32), ("n2", ctypes.c_int32), ("A", ctypes.c_double * 4)]
+
+
+class omni_kernel_stat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 64), ("launches", ctypes.c_int64),
+                ("total_ms", ctypes.c_double), ("bytes", ctypes.c_double)]
+
+
+_lib: Optional[ctypes.CDLL] = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise OSError(f"{path} not found: build it with paper_0909_0001_gb300.build.build()")
+    L = ctypes.CDLL(path)
+    vp, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+    P = ctypes.POINTER
+    lv = P(omni_level)
+    sig = {
+        "omni_lattice_shape": (ctypes.c_int, [lv, ctypes.c_int, P(i64), P(i64)]),
+        "omni_baselines": (ctypes.c_int, [lv, ctypes.c_int, P(i32), P(i64), P(dbl)]),
+        "omni_plan_create": (ctypes.c_int, [lv, ctypes.c_int, i64, ctypes.c_int, ctypes.c_int,
+                                            P(vp)]),
+        "omni_plan_destroy": (None, [vp]),
+        "omni_plan_info": (ctypes.c_int, [vp, P(ctypes.c_int), P(i32), P(i32), P(i64), P(i64),
+                                          P(i64)]),
+        "omni_correlate": (ctypes.c_int, [vp, vp, i64, vp]),
+        "omni_correlate_host": (ctypes.c_int, [vp, vp, i64, vp]),
+        "omni_visibilities": (ctypes.c_int, [vp, vp, ctypes.c_int, vp]),
+        "omni_visibilities_host": (ctypes.c_int, [vp, vp, ctypes.c_int, vp]),
+        "omni_reset": (ctypes.c_int, [vp, vp]),
+        "omni_sync": (ctypes.c_int, [vp, vp]),
+        "omni_last_error": (ctypes.c_char_p, []),
+        "omni_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+        "omni_profile_enable": (ctypes.c_int, [vp, ctypes.c_int]),
+        "omni_profile_read": (ctypes.c_int, [vp, P(omni_kernel_stat), ctypes.c_int,
+                                             P(ctypes.c_int), ctypes.c_int]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(status: int) -> None:
+    if status != OMNI_OK:
+        raise OmniError(status, load().omni_last_error().decode())
+
+
+def _levels(levels: Sequence[Level]):
+    arr = (omni_level * len(levels))()
+    for k, lv in enumerate(levels):
+        arr[k].n1, arr[k].n2 = int(lv.n1), int(lv.n2)
+        for c in range(4):
+            arr[k].A[c] = float(lv.A[c])
+    return arr
+
+
+def lattice_shape(levels: Sequence[Level]) -> Tuple[int, int]:
+    """(n_antennas, n_lags) of a hierarchy (host only)."""
+    N, Q = ctypes.c_int64(), ctypes.c_int64()
+    _check(load().omni_lattice_shape(_levels(levels), len(levels), ctypes.byref(N),
+                                     ctypes.byref(Q)))
+    return N.value, Q.value
+
+
+def baselines(levels: Sequence[Level]) -> Tuple[np.ndarray, np.ndarray, np.ndarray]:
+    """(dm [Q][2n] int32, redundancy [Q] int64, dr [Q][2] float64), host only."""
+    _, Q = lattice_shape(levels)
+    D = 2 * len(levels)
+    dm = np.zeros((Q, D), dtype=np.int32)
+    red = np.zeros(Q, dtype=np.int64)
+    dr = np.zeros((Q, 2), dtype=np.float64)
+    _check(load().omni_baselines(
+        _levels(levels), len(levels), dm.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+        red.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+        dr.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return dm, red, dr
+
+
+def _stream_ptr(stream) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(int(stream.cuda_stream))
+
+
+class Plan:
+    """A correlator plan for C channels of one hierarchy (owns device memory)."""
+
+    def __init__(self, levels: Sequence[Level], channels: int, dtype: str = "cf32",
+                 precision: str = "fp32"):
+        self.levels = list(levels)
+        self.channels = int(channels)
+        self.dtype = dtype
+        self.precision = precision
+        h = ctypes.c_void_p()
+        _check(load().omni_plan_create(_levels(levels), len(levels), self.channels,
+                                       DTYPES[dtype], PRECISIONS[precision], ctypes.byref(h)))
+        self._h = h
+        nd = ctypes.c_int()
+        dims = (ctypes.c_int32 * 16)()
+        pad = (ctypes.c_int32 * 16)()
+        N, Q, C = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(load().omni_plan_info(h, ctypes.byref(nd), dims, pad, ctypes.byref(N),
+                                     ctypes.byref(Q), ctypes.byref(C)))
+        self.dims = [dims[d] for d in range(nd.value)]
+        self.padded = [pad[d] for d in range(nd.value)]
+        self.n_antennas = N.value
+        self.n_lags = Q.value
+
+    # ---------------------------------------------------------------- checks
+    def _check_volts(self, v: torch.Tensor) -> int:
+        want = torch.int8 if self.dtype == "ci8" else torch.float32
+        if v.dtype == torch.complex64 and self.dtype == "cf32":
+            v = torch.view_as_real(v)
+        if v.dtype != want:
+            raise TypeError(f"voltages must be {want} [C][T][N][2] for dtype {self.dtype}")
+        if v.dim() != 4 or v.shape[0] != self.channels or v.shape[2] != self.n_antennas \
+                or v.shape[3] != 2:
+            raise ValueError(f"voltages must have shape [{self.channels}][T][{self.n_antennas}][2],"
+                             f" got {tuple(v.shape)}")
+        if not v.is_contiguous():
+            raise ValueError("voltages must be contiguous")
+        return int(v.shape[1])
+
+    # ---------------------------------------------------------------- calls
+    def correlate(self, volts: torch.Tensor, stream=None) -> None:
+        """Accumulate |F|^2 of device voltages [C][T][N][2] (async on stream)."""
+        if not volts.is_cuda:
+            raise ValueError("correlate() takes device voltages; use correlate_host()")
+        T = self._check_volts(volts)
+        _check(load().omni_correlate(self._h, ctypes.c_void_p(volts.data_ptr()), T,
+                                     _stream_ptr(stream)))
+
+    def correlate_host(self, volts: torch.Tensor, stream=None) -> None:
+        """Accumulate host voltages (copied in chunks, overlapped with the transforms)."""
+        if volts.is_cuda:
+            raise ValueError("correlate_host() takes host voltages")
+        T = self._check_volts(volts)
+        _check(load().omni_correlate_host(self._h, ctypes.c_void_p(volts.data_ptr()), T,
+                                          _stream_ptr(stream)))
+
+    def visibilities(self, reset: bool = True, out: Optional[torch.Tensor] = None,
+                     stream=None) -> torch.Tensor:
+        """Visibilities [C][Q] complex128 on the device."""
+        if out is None:
+            out = torch.empty((self.channels, self.n_lags), dtype=torch.complex128, device="cuda")
+        if out.dtype != torch.complex128 or not out.is_cuda or not out.is_contiguous() \
+                or out.numel() != self.channels * self.n_lags:
+            raise ValueError("out must be a contiguous complex128 CUDA tensor of C*Q elements")
+        _check(load().omni_visibilities(self._h, ctypes.c_void_p(out.data_ptr()), int(reset),
+                                        _stream_ptr(stream)))
+        return out
+
+    def visibilities_host(self, reset: bool = True, out: Optional[torch.Tensor] = None,
+                          stream=None) -> torch.Tensor:
+        """Visibilities [C][Q] complex128 copied into host memory."""
+        if out is None:
+            out = torch.empty((self.channels, self.n_lags), dtype=torch.complex128)
+        if out.dtype != torch.complex128 or out.is_cuda or not out.is_contiguous() \
+                or out.numel() != self.channels * self.n_lags:
+            raise ValueError("out must be a contiguous complex128 host tensor of C*Q elements")
+        _check(load().omni_visibilities_host(self._h, ctypes.c_void_p(out.data_ptr()),
+                                             int(reset), _stream_ptr(stream)))
+        return out
+
+    def profile(self, enable: bool = True) -> None:
+        """Record CUDA events around every kernel launch (per-pass timings)."""
+        _check(load().omni_profile_enable(self._h, int(enable)))
+
+    def kernel_stats(self, clear: bool = False) -> list:
+        """Per-pass [{name, launches, total_ms, bytes}] (waits for recorded events)."""
+        n = ctypes.c_int()
+        _check(load().omni_profile_read(self._h, None, 0, ctypes.byref(n), 0))
+        arr = (omni_kernel_stat * max(1, n.value))()
+        _check(load().omni_profile_read(self._h, arr, n.value, ctypes.byref(n), int(clear)))
+        return [{"name": arr[i].name.decode(), "launches": arr[i].launches,
+                 "total_ms": arr[i].total_ms, "bytes": arr[i].bytes} for i in range(n.value)]
+
+    def reset(self, stream=None) -> None:
+        _check(load().omni_reset(self._h, _stream_ptr(stream)))
+
+    def sync(self, stream=None) -> None:
+        _check(load().omni_sync(self._h, _stream_ptr(stream)))
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().omni_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

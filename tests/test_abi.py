@@ -1,0 +1,111 @@
+"""CPU-only checks of the C ABI: the library loads, exports every declared entry
+point, and its host-side tables match the oracle bit for bit."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import oracle
+from paper_0909_0001_gb300 import omni, synth
+from paper_0909_0001_gb300.build import INCLUDE, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build()
+    return omni.load()
+
+
+def declared_entry_points():
+    names = set()
+    for h in os.listdir(INCLUDE):
+        if h.endswith(".h"):
+            text = open(os.path.join(INCLUDE, h)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(omni_[a-z_]+)\s*\(", text))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_entry_points()
+    assert "omni_correlate" in names and "omni_plan_create" in names
+    for name in names:
+        assert hasattr(lib, name), f"{name} declared in include/ but not exported"
+    assert set(omni.EXPORTS) <= set(names)
+
+
+LAYOUTS = {
+    "warmup_2level": synth.paper_fixture("warmup_2level"),
+    "three_level": synth.paper_fixture("three_level"),
+    "blocks": synth.paper_fixture("blocks"),
+    "interleaved": synth.paper_fixture("interleaved"),
+    "sheared": synth.hierarchy([(5, 3), (3, 4), (2, 2)], [0.2, 1.3, 2.9], [0.1, -0.2, 0.25]),
+    "hier2": synth.workload("hier2").levels,
+}
+
+
+@pytest.mark.parametrize("name", sorted(LAYOUTS))
+def test_baseline_tables_match_oracle(lib, name):
+    levels = LAYOUTS[name]
+    dims = synth.lattice_dims(levels)
+    dm, red, dr = omni.baselines(levels)
+    odm, ored = oracle.lag_table(dims)
+    np.testing.assert_array_equal(dm, odm)
+    np.testing.assert_array_equal(red, ored)
+    np.testing.assert_allclose(dr, oracle.baseline_vectors(levels, odm), rtol=0, atol=1e-9)
+    N, Q = omni.lattice_shape(levels)
+    assert N == int(np.prod(dims)) and Q == len(odm)
+
+
+def test_collision_verdicts_match_oracle(lib):
+    ok = [synth.paper_fixture("interleaved"), synth.paper_fixture("three_level"),
+          synth.paper_fixture("warmup_2level"), [synth.Level(1, 1)]]
+    bad = [[synth.Level(4, 1, (1, 0, 0, 1)), synth.Level(2, 1, (2, 0, 0, 1))],
+           [synth.Level(3, 3, (1, 0, 0, 1)), synth.Level(2, 2, (0, 0, 0, 0))],
+           [synth.Level(2, 1, (0, 0, 0, 0))]]
+    for levels in ok + bad:
+        expect = oracle.collides(levels)
+        if expect:
+            with pytest.raises(omni.OmniError) as e:
+                omni.baselines(levels)
+            assert e.value.status == 2
+        else:
+            omni.baselines(levels)
+    assert not any(oracle.collides(lv) for lv in ok)
+    assert all(oracle.collides(lv) for lv in bad)
+
+
+@pytest.mark.parametrize("levels, status", [
+    ([], 1),
+    ([synth.Level(0, 3)], 1),
+    ([synth.Level(3, -1)], 1),
+    ([synth.Level(3, 3, (float("nan"), 0, 0, 1))], 1),
+    ([synth.Level(4096, 2)], 3),        # padded axis 8192 > 4096
+    ([synth.Level(513, 2)], 3),         # padded axis 1026: not a power of two and > 1024
+    ([synth.Level(2, 2)] * 9, 1),       # more than 8 levels
+])
+def test_invalid_hierarchies_are_rejected(lib, levels, status):
+    with pytest.raises(omni.OmniError) as e:
+        omni.lattice_shape(levels)
+    assert e.value.status == status
+    assert omni.load().omni_last_error()
+
+
+def test_status_strings(lib):
+    for code, name in omni.STATUS_NAMES.items():
+        assert lib.omni_status_string(code).decode() == name
+
+
+def test_plan_create_rejects_bad_arguments_without_touching_the_gpu(lib):
+    import ctypes
+    h = ctypes.c_void_p()
+    lv = omni._levels([synth.Level(4, 4)])
+    assert lib.omni_plan_create(lv, 1, 0, 0, 0, ctypes.byref(h)) == 1       # no channels
+    assert lib.omni_plan_create(lv, 1, 1, 7, 0, ctypes.byref(h)) == 1       # bad dtype
+    assert lib.omni_plan_create(lv, 1, 1, 0, 9, ctypes.byref(h)) == 1       # bad precision
+    assert lib.omni_plan_create(lv, 1, 1, 0, 0, None) == 1                  # no out pointer
+    assert lib.omni_correlate(None, None, 1, None) == 1
+    assert lib.omni_visibilities(None, None, 1, None) == 1

@@ -1,0 +1,228 @@
+"""GPU parity: the CUDA correlator (through the C ABI) against the CPU FP64 oracle.
+
+Bar (FP32 path): relative Frobenius error of the visibilities <= 1e-5 per
+channel; integer results (baseline indices, all-ones redundancy counts after
+rounding, the paper's warm-up example) exact.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from conftest import read_golden
+from oracle import oracle
+from paper_0909_0001_gb300 import omni, synth
+
+pytestmark = pytest.mark.gpu
+
+TOL_FP32 = 1e-5
+
+
+def gpu_vis(levels, x, dtype="cf32", calls=None):
+    """Visibilities [C][Q] from the CUDA library for voltages x [C][T][N][2]."""
+    C = x.shape[0]
+    with omni.Plan(levels, C, dtype=dtype) as plan:
+        xd = x.cuda()
+        if calls is None:
+            plan.correlate(xd)
+        else:
+            t0 = 0
+            for t in calls:
+                plan.correlate(xd[:, t0:t0 + t].contiguous())
+                t0 += t
+        return plan.visibilities().cpu().numpy()
+
+
+def relerr_per_channel(V, ref):
+    num = np.linalg.norm(V - ref, axis=1)
+    den = np.maximum(np.linalg.norm(ref, axis=1), 1e-300)
+    return float(np.max(num / den))
+
+
+def check(levels, x, dtype="cf32", tol=TOL_FP32):
+    V = gpu_vis(levels, x, dtype)
+    ref = oracle.correlate(synth.lattice_dims(levels), x)
+    err = relerr_per_channel(V, ref)
+    assert err <= tol, f"relative Frobenius error {err:.3e} > {tol:g}"
+    return V, ref
+
+
+# ---------------------------------------------------------------- paper values
+
+def test_warmup_example_is_exact():
+    g = read_golden("warmup_example.txt")
+    f = np.array(g["voltages"][0], dtype=np.float32)
+    x1 = torch.zeros((1, 1, 9, 2))
+    x1[0, 0, [0, 1, 2, 6, 7, 8], 0] = torch.from_numpy(f)
+    V1 = gpu_vis(synth.paper_fixture("warmup_1d"), x1)
+    np.testing.assert_array_equal(np.rint(V1.real[0]), g["g_1d"][0])
+    assert np.max(np.abs(V1[0] - np.array(g["g_1d"][0]))) < 1e-4
+    x2 = torch.zeros((1, 1, 6, 2))
+    x2[0, 0, :, 0] = torch.from_numpy(f)
+    V2 = gpu_vis(synth.paper_fixture("warmup_2level"), x2)
+    np.testing.assert_array_equal(np.rint(V2.real[0]).reshape(3, 5), np.array(g["G_2d_row"]))
+
+
+@pytest.mark.parametrize("name,T", [("three_level", 3), ("blocks", 2), ("interleaved", 4),
+                                    ("plank", 1), ("strips", 1), ("warmup_2level", 5)])
+def test_paper_layouts(name, T):
+    levels = synth.paper_fixture(name)
+    x = synth.random_complex(synth.lattice_dims(levels), 1, T, seed=17)
+    check(levels, x)
+
+
+@pytest.mark.parametrize("levels", [
+    synth.paper_fixture("blocks"),
+    [synth.Level(16, 16)],
+    synth.hierarchy([(4, 3), (3, 2), (2, 2)], [0.3, 1.0, 2.0], [0.1, 0.2, -0.2]),
+    [synth.Level(1, 1)],
+])
+def test_all_ones_gives_exact_redundancy(levels):
+    dims = synth.lattice_dims(levels)
+    T = 2
+    V = gpu_vis(levels, synth.all_ones(dims, 1, T))
+    _, red, _ = omni.baselines(levels)
+    np.testing.assert_array_equal(np.rint(V.real[0]).astype(np.int64), T * red)
+    assert np.max(np.abs(V[0] - T * red)) < 1e-3 * max(1, T * red.max()) ** 0.5
+
+
+# ---------------------------------------------------------------- workloads
+
+def test_grid16_full_size():
+    w = synth.workload("grid16")
+    x = synth.voltages(w)
+    check(w.levels, x)
+
+
+def test_hier2_reduced_ragged_chunks_int8():
+    w = synth.workload("hier2")
+    x = synth.voltages(w, channels=3, samples=5)
+    check(w.levels, x, dtype="ci8")
+
+
+def test_hier3_small_six_dims():
+    levels = synth.hierarchy([(4, 4), (4, 2), (2, 3)], [0.5, 1.5, 2.5], [0.2, -0.1, 0.3])
+    x = synth.random_complex(synth.lattice_dims(levels), 2, 3, seed=5)
+    check(levels, x)
+
+
+def sampled_error(levels, x, V, chans, lags):
+    """Frobenius error estimated from sampled lags: sqrt(Q mean|dV|^2) / ||V_gpu||."""
+    ref = oracle.correlate_selected(synth.lattice_dims(levels), x, chans, lags)
+    got = V[chans, lags]
+    Q = V.shape[1]
+    errs = []
+    for c in np.unique(chans):
+        m = chans == c
+        est = math.sqrt(Q * np.mean(np.abs(got[m] - ref[m]) ** 2)) / np.linalg.norm(V[c])
+        errs.append(est)
+    return max(errs), got, ref
+
+
+def property_checks(levels, x, V, tol=TOL_FP32):
+    """Size-independent properties: V(0) = sum|x|^2 (Parseval), V(-D) = conj V(D)."""
+    power = np.array([float((x[c].double() ** 2).sum()) for c in range(x.shape[0])])
+    zero = V.shape[1] // 2
+    np.testing.assert_allclose(V[:, zero].real, power, rtol=tol)
+    herm = np.linalg.norm(V[:, ::-1] - np.conj(V), axis=1) / np.linalg.norm(V, axis=1)
+    assert herm.max() <= tol
+
+
+def test_hier3_full_lattice_sampled():
+    w = synth.workload("hier3")
+    x = synth.voltages(w, channels=1, samples=2)
+    V = gpu_vis(w.levels, x)
+    rng = np.random.default_rng(3)
+    lags = np.concatenate([[V.shape[1] // 2, 0, V.shape[1] - 1], rng.integers(0, V.shape[1], 253)])
+    err, _, _ = sampled_error(w.levels, x, V, np.zeros_like(lags), lags)
+    assert err <= TOL_FP32, err
+    property_checks(w.levels, x, V)
+
+
+def test_grid1024_sampled():
+    w = synth.workload("grid1024")
+    x = synth.voltages(w, channels=1, samples=2)
+    V = gpu_vis(w.levels, x)
+    rng = np.random.default_rng(4)
+    lags = np.concatenate([[V.shape[1] // 2], rng.integers(0, V.shape[1], 511)])
+    err, _, _ = sampled_error(w.levels, x, V, np.zeros_like(lags), lags)
+    assert err <= TOL_FP32, err
+    property_checks(w.levels, x, V)
+
+
+def test_hier2_full_size_sampled():
+    """The benchmark configuration: 64 channels x 1024 samples of int8 voltages."""
+    w = synth.workload("hier2")
+    xd = synth.voltages(w, device="cuda")
+    with omni.Plan(w.levels, w.channels, dtype=w.dtype) as plan:
+        plan.correlate(xd)
+        V = plan.visibilities().cpu().numpy()
+    x = xd.cpu()
+    del xd
+    rng = np.random.default_rng(5)
+    chans = np.repeat(np.array([0, 37, 63]), 96)
+    lags = rng.integers(0, V.shape[1], chans.size)
+    lags[::96] = V.shape[1] // 2
+    err, _, _ = sampled_error(w.levels, x, V, chans, lags)
+    assert err <= TOL_FP32, err
+    property_checks(w.levels, x, V)
+
+
+# ---------------------------------------------------------------- API semantics
+
+def test_split_calls_equal_one_call_and_reset():
+    levels = synth.hierarchy([(8, 4), (4, 4)], [0.0, 0.7], [0.0, 0.15])
+    x = synth.random_complex(synth.lattice_dims(levels), 2, 12, seed=8)
+    one = gpu_vis(levels, x)
+    split = gpu_vis(levels, x, calls=[5, 0, 7])
+    assert relerr_per_channel(split, one) <= 1e-6
+    with omni.Plan(levels, 2) as plan:
+        plan.correlate(synth.random_complex(synth.lattice_dims(levels), 2, 3, seed=99).cuda())
+        plan.visibilities(reset=True)            # discards the first integration
+        plan.correlate(x.cuda())
+        again = plan.visibilities(reset=True).cpu().numpy()
+    assert relerr_per_channel(again, one) <= 1e-6
+
+
+def test_host_path_matches_device_path():
+    w = synth.workload("hier2")
+    x = synth.voltages(w, channels=2, samples=40)
+    dev = gpu_vis(w.levels, x, dtype="ci8")
+    with omni.Plan(w.levels, 2, dtype="ci8") as plan:
+        plan.correlate_host(x.pin_memory())
+        host = plan.visibilities_host().numpy()
+        plan.correlate_host(x)                   # pageable memory works too
+        host2 = plan.visibilities_host().numpy()
+    np.testing.assert_array_equal(host, dev)
+    np.testing.assert_array_equal(host2, dev)
+
+
+@pytest.mark.parametrize("levels", [
+    [synth.Level(1, 1)],
+    [synth.Level(16, 1)],
+    [synth.Level(1, 16)],
+    [synth.Level(1, 1), synth.Level(5, 1, (3.0, 0.0, 0.0, 1.0))],
+    [synth.Level(3, 5)],
+    [synth.Level(7, 2), synth.Level(3, 1, (7.0, 0.0, 0.0, 2.0))],
+    [synth.Level(100, 3)],
+])
+def test_degenerate_and_odd_shapes(levels):
+    x = synth.random_complex(synth.lattice_dims(levels), 2, 3, seed=12)
+    check(levels, x)
+
+
+def test_zero_samples_is_a_no_op():
+    levels = [synth.Level(4, 4)]
+    with omni.Plan(levels, 1) as plan:
+        plan.correlate(torch.zeros((1, 0, 16, 2), device="cuda"))
+        V = plan.visibilities().cpu().numpy()
+    assert np.all(V == 0)
+
+
+def test_wrong_input_is_rejected():
+    with omni.Plan([synth.Level(4, 4)], 2) as plan:
+        with pytest.raises(ValueError):
+            plan.correlate(torch.zeros((1, 3, 16, 2), device="cuda"))
+        with pytest.raises(TypeError):
+            plan.correlate(torch.zeros((2, 3, 16, 2), dtype=torch.int8, device="cuda"))
