@@ -159,6 +159,39 @@ omni_status omni_profile_enable(omni_plan* plan, int enable);
 omni_status omni_profile_read(omni_plan* plan, omni_kernel_stat* out, int max, int* n_out,
                               int clear);
 
+/* Size of the device array that omni_correlate_noalloc uses as scratch. */
+#define OMNI_NOALLOC_SCRATCH_BYTES (64ull * 1024ull * 1024ull)
+
+/* One whole integration without any device allocation.  The paper has no
+ * counterpart: this is for callers that cannot call cudaMalloc, such as code
+ * running under another framework's memory pool or allocator hooks, processes
+ * that reserve all device memory up front, and real-time pipelines that forbid
+ * allocation after start-up.
+ *
+ * Computes the visibilities of T samples of C channels of a hierarchy, exactly
+ * as omni_plan_create + omni_correlate + omni_visibilities would, and returns
+ * after they are written.  volts_dev: DEVICE [C][T][N] complex voltages of
+ * dtype (16-byte aligned, read only); vis_dev: DEVICE [C][n_lags] complex128
+ * output (16-byte aligned).  Both belong to the caller.
+ *
+ * Scratch (the FP64 accumulator, the pass buffers, the direct-DFT twiddles) is
+ * one static device array of OMNI_NOALLOC_SCRATCH_BYTES (64 MiB) inside the
+ * library; every GPU that loads this part of the library holds it until the
+ * process exits.  The call allocates nothing: no cudaMalloc, no cudaFree.  A
+ * problem whose scratch (C x L x 8 bytes of accumulator plus two pass buffers
+ * of at least one sample or channel each) does not fit returns
+ * OMNI_ERR_UNSUPPORTED with the sizes in omni_last_error().
+ *
+ * The first call on each device does the set-up (uploads the twiddle tables
+ * and looks up the array's device address), so make that first call before
+ * any stream capture.  Every call shares the one array and the accumulator is
+ * cleared at the start of each call: calls that overlap on the GPU (other
+ * streams, other host threads) race on it and must be serialised by the
+ * caller.  Synchronises stream before returning. */
+omni_status omni_correlate_noalloc(const omni_level* levels, int n_levels, int64_t n_channels,
+                                   omni_dtype dtype, const void* volts_dev, int64_t T,
+                                   double* vis_dev, void* stream);
+
 /* Message describing the calling thread's most recent failure ("" if none). */
 const char* omni_last_error(void);
 

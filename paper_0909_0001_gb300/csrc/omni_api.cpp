@@ -154,6 +154,8 @@ omni_status check_unique(const Geometry& g) {
 
 }  // namespace
 
+void omni::set_last_error(const char* msg) { g_last_error = msg; }
+
 // ----------------------------------------------------------------------------- plan
 
 struct omni_plan {

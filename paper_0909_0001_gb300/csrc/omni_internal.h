@@ -74,4 +74,7 @@ cudaError_t init_device_tables();
 // Launch one pass on stream.
 cudaError_t launch_pass(const Pass& p, const PassArgs& a, cudaStream_t stream);
 
+// Set the calling thread's omni_last_error() message.
+void set_last_error(const char* msg);
+
 }  // namespace omni

@@ -31,7 +31,7 @@ EXPORTS = (
     "omni_lattice_shape", "omni_baselines", "omni_plan_create", "omni_plan_destroy",
     "omni_plan_info", "omni_correlate", "omni_correlate_host", "omni_visibilities",
     "omni_visibilities_host", "omni_reset", "omni_sync", "omni_last_error",
-    "omni_status_string", "omni_profile_enable", "omni_profile_read",
+    "omni_status_string", "omni_profile_enable", "omni_profile_read", "omni_correlate_noalloc",
 )
 
 
@@ -81,6 +81,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "omni_last_error": (ctypes.c_char_p, []),
         "omni_status_string": (ctypes.c_char_p, [ctypes.c_int]),
         "omni_profile_enable": (ctypes.c_int, [vp, ctypes.c_int]),
+        "omni_correlate_noalloc": (ctypes.c_int, [lv, ctypes.c_int, i64, ctypes.c_int, vp, i64,
+                                                  vp, vp]),
         "omni_profile_read": (ctypes.c_int, [vp, P(omni_kernel_stat), ctypes.c_int,
                                              P(ctypes.c_int), ctypes.c_int]),
     }
@@ -126,6 +128,22 @@ def baselines(levels: Sequence[Level]) -> Tuple[np.ndarray, np.ndarray, np.ndarr
         red.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
         dr.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
     return dm, red, dr
+
+
+def correlate_noalloc(levels: Sequence[Level], volts: torch.Tensor, dtype: str,
+                      out: torch.Tensor, stream=None) -> torch.Tensor:
+    """One integration through omni_correlate_noalloc, which allocates no device
+    memory (for callers that cannot allocate; see include/omni.h).  volts:
+    contiguous device [C][T][N][2]; out: contiguous device complex128 [C][Q]."""
+    if not (volts.is_cuda and out.is_cuda and volts.is_contiguous() and out.is_contiguous()):
+        raise ValueError("volts and out must be contiguous CUDA tensors")
+    if out.dtype != torch.complex128:
+        raise TypeError("out must be complex128")
+    C, T = int(volts.shape[0]), int(volts.shape[1])
+    _check(load().omni_correlate_noalloc(_levels(levels), len(levels), C, DTYPES[dtype],
+                                         ctypes.c_void_p(volts.data_ptr()), T,
+                                         ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+    return out
 
 
 def _stream_ptr(stream) -> ctypes.c_void_p:
