@@ -230,29 +230,58 @@ void choose_kind(Pass& p) {
     }
 }
 
+// Level pass tiling (fixed at compile time in the kernels): the finest level
+// (inner == 1) packs whole blocks, W = 1; a coarser level takes W consecutive
+// inner indices, W = 256 * LPT / L with LPT = 2 lines per thread (1 for
+// 64-point axes) in a LAST pass and 1 in a MID pass.
+void choose_level(Pass& p) {
+    p.kind = KIND_LEVEL;
+    const int lpt = p.mode == MODE_LAST ? (p.L >= 64 ? 1 : 2) : 1;
+    p.W = p.inner == 1 ? 1 : 256 * lpt / p.L;
+}
+
 omni_status build_passes(omni_plan* pl) {
     const Geometry& g = pl->g;
     std::vector<int> axes;
     for (int d = 0; d < g.D; ++d)
         if (g.Lp[d] > 1) axes.push_back(d);
     if (axes.empty()) axes.push_back(0);  // a single antenna: an identity "transform"
-    // forward: increasing axis order; inputs [outer n_e>d][n_d][inner L_e<d]
-    pl->fwd.clear();
-    pl->fwd_elems = 0;
+    // forward: increasing axis order; inputs [outer n_e>d][n_d][inner L_e<d].
+    // A level whose two axes have the same power-of-two padded length <= 64 is
+    // transformed by one level pass (both axes in shared memory); other axes
+    // get one pass each.  OMNI_LEVEL_PASSES=0 forces one pass per axis.
+    bool use_level = true;
+    if (const char* env = std::getenv("OMNI_LEVEL_PASSES")) use_level = std::atoi(env) != 0;
+    std::vector<std::pair<int, bool>> stages;  // (first axis, is a level pass)
     for (size_t a = 0; a < axes.size(); ++a) {
         const int d = axes[a];
+        const bool pair = use_level && (d % 2 == 0) && a + 1 < axes.size() && axes[a + 1] == d + 1 &&
+                          g.Lp[d] == g.Lp[d + 1] && is_pow2(g.Lp[d]) && g.Lp[d] <= 64;
+        stages.push_back({d, pair});
+        if (pair) ++a;
+    }
+    pl->fwd.clear();
+    pl->fwd_elems = 0;
+    for (size_t k = 0; k < stages.size(); ++k) {
+        const int d = stages[k].first;
+        const bool level = stages[k].second;
+        const int last_axis = level ? d + 1 : d;
         Pass p{};
         p.axis = d;
         p.L = g.Lp[d];
         p.n = g.n[d];
-        p.q_out = g.Lp[d];
+        p.q_out = level ? g.Lp[d] * g.Lp[d] : g.Lp[d];
         p.inner = 1;
         p.outer = 1;
         for (int e = 0; e < d; ++e) p.inner *= g.Lp[e];
-        for (int e = d + 1; e < g.D; ++e) p.outer *= g.n[e];
-        p.mode = (a + 1 == axes.size()) ? MODE_LAST : MODE_MID;
-        choose_kind(p);
-        if (p.mode == MODE_MID) pl->fwd_elems = std::max(pl->fwd_elems, p.outer * p.L * p.inner);
+        for (int e = last_axis + 1; e < g.D; ++e) p.outer *= g.n[e];
+        p.mode = (k + 1 == stages.size()) ? MODE_LAST : MODE_MID;
+        if (level) {
+            choose_level(p);
+        } else {
+            choose_kind(p);
+        }
+        if (p.mode == MODE_MID) pl->fwd_elems = std::max(pl->fwd_elems, p.outer * p.q_out * p.inner);
         pl->fwd.push_back(p);
     }
     // inverse: decreasing axis order; inputs [outer Q_e>d][L_d][inner L_e<d]
@@ -294,16 +323,34 @@ omni_status build_passes(omni_plan* pl) {
     return OMNI_OK;
 }
 
-// Chunk sizes: each scratch buffer holds about OMNI_CHUNK_MB (default 48) MB
-// so a chunk's intermediates stay in L2, and the last pass gets at least ~64K
-// lines of parallel work.
+// Chunk sizes: the last pass gets one wave of resident CTAs (channels x inner
+// tiles), and each scratch buffer holds about OMNI_CHUNK_MB (default 192) MB of
+// samples: long chunks amortise the FP64 fold and the launch ramp better than
+// L2-sized ones (measured on the 2-level workload: 48 MB 48.6 ms, 96 MB 38.0 ms,
+// 192 MB 29.9 ms per step).
 void choose_chunks(omni_plan* pl) {
-    int64_t mb = 48;
+    int64_t mb = 192;
     if (const char* env = std::getenv("OMNI_CHUNK_MB")) mb = std::max<int64_t>(1, std::atoll(env));
     const int64_t target = mb << 20;
+    // CTAs the last pass runs per channel of a chunk
     const Pass& last = pl->fwd.back();
-    const int64_t last_lines = std::max<int64_t>(1, last.inner);
-    pl->Cc = std::min<int64_t>(pl->C, std::max<int64_t>(1, (65536 + last_lines - 1) / last_lines));
+    int64_t ctas = 1;
+    switch (last.kind) {
+        case KIND_LEVEL:
+        case KIND_SMEM: ctas = (last.inner + last.W - 1) / last.W; break;
+        case KIND_REG: ctas = (last.inner + 255) / 256; break;
+        default: ctas = (last.L * last.inner + 255) / 256; break;
+    }
+    // resident CTA slots of the GPU for that kernel
+    int sms = 0, per_sm = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, pl->device) != cudaSuccess) sms = 0;
+    const int first_src = pl->fwd.size() == 1 ? (pl->dtype == OMNI_IN_CI8 ? SRC_CI8 : SRC_CF32) : SRC_BUF;
+    if (last.kind == KIND_LEVEL && level_last_occupancy(last, first_src, &per_sm) != cudaSuccess) per_sm = 0;
+    cudaGetLastError();
+    int64_t slots = (int64_t)std::max(sms, 1) * std::max(per_sm, 2);
+    if (sms <= 0) slots = 304;
+    // fill one wave of the last pass: as many channels as the slots hold
+    pl->Cc = std::min<int64_t>(pl->C, std::max<int64_t>(1, slots / ctas));
     const int64_t per_sample = std::max<int64_t>(1, pl->fwd_elems) * (int64_t)sizeof(float2);
     const int64_t samples = std::max<int64_t>(1, target / per_sample);
     pl->Tc = std::max<int64_t>(1, std::min<int64_t>(1024, samples / pl->Cc));
@@ -334,7 +381,9 @@ void release(omni_plan* pl) {
     delete pl;
 }
 
-const char* kind_name(int k) { return k == KIND_REG ? "reg" : k == KIND_SMEM ? "smem" : "direct"; }
+const char* kind_name(int k) {
+    return k == KIND_REG ? "reg" : k == KIND_SMEM ? "smem" : k == KIND_LEVEL ? "level" : "direct";
+}
 const char* mode_name(int m) {
     return m == MODE_MID ? "mid" : m == MODE_LAST ? "last" : m == MODE_INV_MID ? "mid" : "last";
 }
@@ -344,8 +393,12 @@ void init_stats(omni_plan* pl) {
     for (int inv = 0; inv < 2; ++inv)
         for (const Pass& p : inv ? pl->inv : pl->fwd) {
             omni_kernel_stat st{};
-            snprintf(st.name, sizeof st.name, "%s axis%d %s%d %s", inv ? "inv" : "fwd", p.axis,
-                     kind_name(p.kind), p.L, mode_name(p.mode));
+            if (p.kind == KIND_LEVEL)
+                snprintf(st.name, sizeof st.name, "%s axis%d+%d %s%d %s", inv ? "inv" : "fwd", p.axis,
+                         p.axis + 1, kind_name(p.kind), p.L, mode_name(p.mode));
+            else
+                snprintf(st.name, sizeof st.name, "%s axis%d %s%d %s", inv ? "inv" : "fwd", p.axis,
+                         kind_name(p.kind), p.L, mode_name(p.mode));
             pl->stats.push_back(st);
         }
 }
@@ -369,11 +422,12 @@ double src_bytes(int src_kind) {
 // Algorithmic bytes of one launch: inputs read plus outputs written.
 double pass_bytes(const Pass& p, const PassArgs& a) {
     const double in = src_bytes(a.src_kind);
+    const double n_in = p.kind == KIND_LEVEL ? (double)p.n * p.n : (double)p.n;
     switch (p.mode) {
         case MODE_MID:
-            return (double)a.S * p.outer * p.inner * (p.n * in + p.L * 8.0);
+            return (double)a.S * p.outer * p.inner * (n_in * in + p.q_out * 8.0);
         case MODE_LAST:
-            return (double)a.S * a.tc * p.inner * p.n * in + (double)a.S * p.L * p.inner * 16.0;
+            return (double)a.S * a.tc * p.inner * n_in * in + (double)a.S * p.q_out * p.inner * 16.0;
         case MODE_INV_MID:
             return (double)a.S * p.outer * p.inner * (p.n * in + p.q_out * 8.0);
         default:
@@ -423,13 +477,13 @@ omni_status run_chunk(omni_plan* pl, const void* volts, int64_t vc0, int64_t Tsr
         } else {
             a.S = cc * tc;
             a.dst = dst;
-            a.dst_stride = p.outer * p.L * p.inner;
+            a.dst_stride = p.outer * p.q_out * p.inner;
         }
         cudaError_t e = launch_counted(pl, (int)k, p, a, st);
         if (e != cudaSuccess) return cuda_fail(e, "forward pass launch");
         src = dst;
         src_kind = SRC_BUF;
-        src_stride = p.outer * p.L * p.inner;
+        src_stride = p.outer * p.q_out * p.inner;
     }
     return OMNI_OK;
 }

@@ -13,11 +13,17 @@ cudaError_t launch_smem_a(const Pass& p, const PassArgs& a, cudaStream_t st);
 cudaError_t launch_smem_b(const Pass& p, const PassArgs& a, cudaStream_t st);
 cudaError_t launch_smem_c(const Pass& p, const PassArgs& a, cudaStream_t st);
 cudaError_t launch_direct(const Pass& p, const PassArgs& a, cudaStream_t st);
+cudaError_t launch_level_a(const Pass& p, const PassArgs& a, cudaStream_t st);
+cudaError_t launch_level_b(const Pass& p, const PassArgs& a, cudaStream_t st);
+cudaError_t level_occupancy_a(int L, bool finest, int src_kind, int* out);
+cudaError_t level_occupancy_b(int L, bool finest, int src_kind, int* out);
 cudaError_t upload_twiddles_reg_a();
 cudaError_t upload_twiddles_reg_b();
 cudaError_t upload_twiddles_smem_a();
 cudaError_t upload_twiddles_smem_b();
 cudaError_t upload_twiddles_smem_c();
+cudaError_t upload_twiddles_level_a();
+cudaError_t upload_twiddles_level_b();
 
 cudaError_t launch_pass(const Pass& p, const PassArgs& a, cudaStream_t st) {
     switch (p.kind) {
@@ -25,8 +31,14 @@ cudaError_t launch_pass(const Pass& p, const PassArgs& a, cudaStream_t st) {
         case KIND_SMEM:
             return p.L <= 512 ? launch_smem_a(p, a, st)
                  : p.L <= 2048 ? launch_smem_b(p, a, st) : launch_smem_c(p, a, st);
+        case KIND_LEVEL: return p.L <= 16 ? launch_level_a(p, a, st) : launch_level_b(p, a, st);
         default: return launch_direct(p, a, st);
     }
+}
+
+cudaError_t level_last_occupancy(const Pass& p, int src_kind, int* blocks_per_sm) {
+    return p.L <= 16 ? level_occupancy_a(p.L, p.inner == 1, src_kind, blocks_per_sm)
+                     : level_occupancy_b(p.L, p.inner == 1, src_kind, blocks_per_sm);
 }
 
 cudaError_t init_device_tables() {
@@ -39,7 +51,8 @@ cudaError_t init_device_tables() {
     for (int d : done)
         if (d == dev) return cudaSuccess;
     for (auto up : {upload_twiddles_reg_a, upload_twiddles_reg_b, upload_twiddles_smem_a,
-                    upload_twiddles_smem_b, upload_twiddles_smem_c})
+                    upload_twiddles_smem_b, upload_twiddles_smem_c, upload_twiddles_level_a,
+                    upload_twiddles_level_b})
         if ((e = up()) != cudaSuccess) return e;
     done.push_back(dev);
     return cudaSuccess;

@@ -29,12 +29,15 @@ enum PassMode : int {
 enum PassKind : int {
     KIND_REG = 0,    // whole line in one thread's registers (power of two <= 64)
     KIND_SMEM = 1,   // four-step L = L1 * L2 through shared memory (power of two <= 4096)
-    KIND_DIRECT = 2  // direct DFT from a twiddle table (any length)
+    KIND_DIRECT = 2, // direct DFT from a twiddle table (any length)
+    KIND_LEVEL = 3   // both axes of one square level (L_a = L_b <= 64) in shared memory
 };
 
 // One axis transform.  The data of one sample (or channel) is viewed as
 // [outer][len][inner] with the transformed axis in the middle: inputs
-// [outer][n][inner], outputs [outer][q_out][inner].
+// [outer][n][inner], outputs [outer][q_out][inner].  A KIND_LEVEL pass
+// transforms two adjacent axes (axis, axis+1) of equal length L at once:
+// [outer][n][n][inner] -> [outer][L][L][inner].
 struct Pass {
     int axis;
     int kind;
@@ -44,7 +47,7 @@ struct Pass {
     int q_out;      // outputs kept per line (L_d forward, 2 n_d - 1 inverse)
     int q_shift;    // inverse: output q holds lag q - q_shift, i.e. bin (q - q_shift) mod L
     int L1, L2;     // KIND_SMEM split
-    int W;          // KIND_SMEM: lines per CTA
+    int W;          // KIND_SMEM / KIND_LEVEL: consecutive inner indices per unit
     int64_t inner, outer;
     const float2* tw;  // KIND_DIRECT: w_L^m = exp(-2 pi i m / L), m < L
 };
@@ -73,6 +76,9 @@ cudaError_t init_device_tables();
 
 // Launch one pass on stream.
 cudaError_t launch_pass(const Pass& p, const PassArgs& a, cudaStream_t stream);
+
+// Resident CTAs per SM of the LAST-mode kernel of a KIND_LEVEL pass.
+cudaError_t level_last_occupancy(const Pass& p, int src_kind, int* blocks_per_sm);
 
 // Set the calling thread's omni_last_error() message.
 void set_last_error(const char* msg);

@@ -226,3 +226,25 @@ def test_wrong_input_is_rejected():
             plan.correlate(torch.zeros((1, 3, 16, 2), device="cuda"))
         with pytest.raises(TypeError):
             plan.correlate(torch.zeros((2, 3, 16, 2), dtype=torch.int8, device="cuda"))
+
+
+# ---------------------------------------------------------------- pass families
+
+@pytest.mark.parametrize("levels, T", [
+    ([synth.Level(32, 32)], 3),                                            # one 64-point level, last
+    (synth.hierarchy([(4, 4), (2, 2), (2, 2)], [0.2, 0.4, 0.6], [0.0, 0.1, 0.2]), 4),
+    (synth.hierarchy([(8, 8), (32, 32)], [0.0, 1.0], [0.0, 0.3]), 1),     # 64-point coarse level
+    (synth.hierarchy([(16, 16), (4, 4)], [0.0, 0.5], [0.0, 0.0]), 3),
+])
+def test_level_pass_shapes(levels, T):
+    x = synth.random_complex(synth.lattice_dims(levels), 2, T, seed=21)
+    check(levels, x)
+
+
+def test_level_and_per_axis_paths_agree(monkeypatch):
+    w = synth.workload("hier2")
+    x = synth.voltages(w, channels=3, samples=20)
+    fused = gpu_vis(w.levels, x, dtype="ci8")
+    monkeypatch.setenv("OMNI_LEVEL_PASSES", "0")
+    per_axis = gpu_vis(w.levels, x, dtype="ci8")
+    assert relerr_per_channel(fused, per_axis) <= 2e-6
