@@ -324,12 +324,12 @@ omni_status build_passes(omni_plan* pl) {
 }
 
 // Chunk sizes: the last pass gets one wave of resident CTAs (channels x inner
-// tiles), and each scratch buffer holds about OMNI_CHUNK_MB (default 192) MB of
+// tiles), and each scratch buffer holds about OMNI_CHUNK_MB (default 384) MB of
 // samples: long chunks amortise the FP64 fold and the launch ramp better than
-// L2-sized ones (measured on the 2-level workload: 48 MB 48.6 ms, 96 MB 38.0 ms,
-// 192 MB 29.9 ms per step).
+// L2-sized ones (measured on the 2-level workload: 96 MB 33.7 ms, 192 MB
+// 26.6 ms, 384 MB 23.4 ms per step).
 void choose_chunks(omni_plan* pl) {
-    int64_t mb = 192;
+    int64_t mb = 384;
     if (const char* env = std::getenv("OMNI_CHUNK_MB")) mb = std::max<int64_t>(1, std::atoll(env));
     const int64_t target = mb << 20;
     // CTAs the last pass runs per channel of a chunk
@@ -617,6 +617,17 @@ omni_status omni_plan_create(const omni_level* levels, int n_levels, int64_t n_c
         return st;
     }
     choose_chunks(pl);
+    // persistent finest-level passes: one wave of resident CTAs
+    for (size_t k = 0; k < pl->fwd.size(); ++k) {
+        Pass& p = pl->fwd[k];
+        if (p.kind != KIND_LEVEL || p.mode != MODE_MID || p.inner != 1) continue;
+        const int src = k == 0 ? (pl->dtype == OMNI_IN_CI8 ? SRC_CI8 : SRC_CF32) : SRC_BUF;
+        int per_sm = 0, sms = 0;
+        if (level_stream_occupancy(p, src, &per_sm) == cudaSuccess &&
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, pl->device) == cudaSuccess)
+            p.grid_cap = per_sm * sms;
+        cudaGetLastError();
+    }
     init_stats(pl);
     const size_t buf_bytes = (size_t)std::max<int64_t>(1, pl->buf_elems) * sizeof(float2);
     const size_t P_bytes = (size_t)pl->C * pl->g.L * sizeof(double);

@@ -17,6 +17,8 @@ cudaError_t launch_level_a(const Pass& p, const PassArgs& a, cudaStream_t st);
 cudaError_t launch_level_b(const Pass& p, const PassArgs& a, cudaStream_t st);
 cudaError_t level_occupancy_a(int L, bool finest, int src_kind, int* out);
 cudaError_t level_occupancy_b(int L, bool finest, int src_kind, int* out);
+cudaError_t level_stream_occupancy_a(int L, int src_kind, int* out);
+cudaError_t level_stream_occupancy_b(int L, int src_kind, int* out);
 cudaError_t upload_twiddles_reg_a();
 cudaError_t upload_twiddles_reg_b();
 cudaError_t upload_twiddles_smem_a();
@@ -39,6 +41,11 @@ cudaError_t launch_pass(const Pass& p, const PassArgs& a, cudaStream_t st) {
 cudaError_t level_last_occupancy(const Pass& p, int src_kind, int* blocks_per_sm) {
     return p.L <= 16 ? level_occupancy_a(p.L, p.inner == 1, src_kind, blocks_per_sm)
                      : level_occupancy_b(p.L, p.inner == 1, src_kind, blocks_per_sm);
+}
+
+cudaError_t level_stream_occupancy(const Pass& p, int src_kind, int* blocks_per_sm) {
+    return p.L <= 16 ? level_stream_occupancy_a(p.L, src_kind, blocks_per_sm)
+                     : level_stream_occupancy_b(p.L, src_kind, blocks_per_sm);
 }
 
 cudaError_t init_device_tables() {

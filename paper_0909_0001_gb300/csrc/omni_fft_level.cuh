@@ -22,6 +22,9 @@
 // current sample is transformed.
 #include "omni_fft_common.cuh"
 
+#include <algorithm>
+#include <type_traits>
+
 namespace omni {
 
 // Compile-time tiling of a level pass of L points per axis.
@@ -199,6 +202,89 @@ level_pass(Pass p, PassArgs a) {
     }
 }
 
+// Finest-level MID pass, persistent: the CTA walks groups of U contiguous
+// blocks (group g, g + gridDim.x, ...), loading the next group two elements
+// per thread per load (4-byte int8 or 16-byte float loads, coalesced) into
+// registers while the current group is transformed.  Requires every group to
+// lie inside one sample (outer % U == 0) and 16-byte aligned group bases.
+template <int L, int SRC>
+__global__ void __launch_bounds__(LevelTile<L, true, MODE_MID>::THREADS)
+level_finest_stream(Pass p, PassArgs a) {
+    using T = LevelTile<L, true, MODE_MID>;
+    constexpr int N = T::N, U = T::U, RP = T::RP, UPL = T::UPL, NT = T::THREADS;
+    constexpr int LOG = ilog2(L);
+    constexpr int PER_GROUP = U * N * N;
+    constexpr int PAIRS = PER_GROUP / 2 / NT;  // two-element loads per thread per group
+    static_assert(PER_GROUP % (2 * NT) == 0, "group must split evenly into pairs");
+    using Pair = typename std::conditional<SRC == SRC_CI8, char4, float4>::type;
+    extern __shared__ float2 sm[];
+    const int64_t groups = a.S * p.outer / U;
+
+    auto group_src = [&](int64_t g) -> const Pair* {
+        const int64_t ug = g * U;                    // first unit: (sample, outer block)
+        const int64_t s = ug / p.outer, o = ug - s * p.outer;
+        return reinterpret_cast<const Pair*>(
+            (SRC == SRC_CI8 ? (const char*)a.src + 2 * (src_base(a, s) + o * N * N)
+                            : (const char*)a.src + 8 * (src_base(a, s) + o * N * N)));
+    };
+    Pair pre[PAIRS];
+    auto fetch = [&](int64_t g) {
+        const Pair* src = group_src(g);
+#pragma unroll
+        for (int q = 0; q < PAIRS; ++q) pre[q] = src[threadIdx.x + q * NT];
+    };
+    int64_t g = blockIdx.x;
+    if (g < groups) fetch(g);
+    for (; g < groups; g += gridDim.x) {
+        // registers -> shared memory ([u][j_b][j_a] with odd row pitch)
+#pragma unroll
+        for (int q = 0; q < PAIRS; ++q) {
+            const int e = 2 * (threadIdx.x + q * NT);
+            const int u = e / (N * N), r = e - u * N * N;
+            const int jb = r / N, ja = r - jb * N;  // ja even: both elements in one row
+            float2 x0, x1;
+            if constexpr (SRC == SRC_CI8) {
+                x0 = make_float2((float)pre[q].x, (float)pre[q].y);
+                x1 = make_float2((float)pre[q].z, (float)pre[q].w);
+            } else {
+                x0 = make_float2(pre[q].x, pre[q].y);
+                x1 = make_float2(pre[q].z, pre[q].w);
+            }
+            float2* d = sm + u * UPL + jb * RP + ja;
+            d[0] = x0;
+            d[1] = x1;
+        }
+        if (g + gridDim.x < groups) fetch(g + gridDim.x);  // in flight during this group
+        __syncthreads();
+        for (int l = threadIdx.x; l < T::LINES_A; l += NT) {
+            const int u = l / N, jb = l - u * N;
+            float2* row = sm + u * UPL + jb * RP;
+            float2 v[L];
+#pragma unroll
+            for (int j = 0; j < L; ++j) v[j] = (j < N) ? row[j] : make_float2(0.f, 0.f);
+            fft_dif<L, true>(v);
+#pragma unroll
+            for (int k = 0; k < L; ++k) row[k] = v[brev(k, LOG)];
+        }
+        __syncthreads();
+        const int64_t ug0 = g * U;
+        const int64_t s = ug0 / p.outer, o0 = ug0 - s * p.outer;
+        float2* dst0 = a.dst + s * a.dst_stride + o0 * (int64_t)L * L;
+        for (int l = threadIdx.x; l < T::LINES_B; l += NT) {
+            const int u = l / L, ka = l - u * L;
+            const float2* col = sm + u * UPL + ka;
+            float2 v[L];
+#pragma unroll
+            for (int j = 0; j < L; ++j) v[j] = (j < N) ? col[j * RP] : make_float2(0.f, 0.f);
+            fft_dif<L, true>(v);
+            float2* d = dst0 + (int64_t)u * L * L + ka;
+#pragma unroll
+            for (int k = 0; k < L; ++k) d[k * L] = v[brev(k, LOG)];
+        }
+        __syncthreads();
+    }
+}
+
 template <int L, bool FINEST, int MODE, int SRC>
 cudaError_t launch_level_t(const Pass& p, const PassArgs& a, cudaStream_t st) {
     using T = LevelTile<L, FINEST, MODE>;
@@ -206,6 +292,22 @@ cudaError_t launch_level_t(const Pass& p, const PassArgs& a, cudaStream_t st) {
     const int64_t blocks = (MODE == MODE_LAST) ? a.S * tiles
                                                : (a.S * p.outer * tiles + T::U - 1) / T::U;
     if (blocks <= 0) return cudaSuccess;
+    if constexpr (FINEST && MODE == MODE_MID && SRC != SRC_P64 && L >= 8) {
+        constexpr int PER_GROUP = T::U * T::N * T::N;
+        const size_t eb = SRC == SRC_CI8 ? 2 : 8;
+        const bool contiguous = p.outer % T::U == 0 && PER_GROUP % (2 * T::THREADS) == 0;
+        const bool aligned = (((uintptr_t)a.src) % 16 == 0) && ((PER_GROUP * eb) % 16 == 0) &&
+                             ((SRC == SRC_BUF ? a.src_stride * eb : a.N * eb) % 16 == 0);
+        if (contiguous && aligned && p.grid_cap > 0) {
+            const int64_t groups = a.S * p.outer / T::U;
+            const int64_t grid = std::min<int64_t>(groups, p.grid_cap);
+            auto ks = level_finest_stream<L, SRC>;
+            cudaError_t e = cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::SMEM);
+            if (e != cudaSuccess) return e;
+            ks<<<(unsigned)grid, T::THREADS, T::SMEM, st>>>(p, a);
+            return cudaGetLastError();
+        }
+    }
     auto k = level_pass<L, FINEST, MODE, SRC>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::SMEM);
     if (e != cudaSuccess) return e;
@@ -226,6 +328,20 @@ cudaError_t launch_level_len(const Pass& p, const PassArgs& a, cudaStream_t st) 
         } else {
             return cudaErrorInvalidValue;
         }
+    });
+}
+
+// Resident CTAs per SM of the finest-level streaming MID pass (host sizing).
+template <int L>
+cudaError_t level_stream_blocks_per_sm(int src_kind, int* out) {
+    *out = 0;
+    if constexpr (L < 8) return cudaSuccess;  // 4-point levels use level_pass
+    else return dispatch_src<MODE_MID>(src_kind, [&](auto S) -> cudaError_t {
+        using T = LevelTile<L, true, MODE_MID>;
+        auto k = level_finest_stream<L, decltype(S)::value>;
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::SMEM);
+        if (e != cudaSuccess) return e;
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k, T::THREADS, T::SMEM);
     });
 }
 

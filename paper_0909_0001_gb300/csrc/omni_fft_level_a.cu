@@ -21,6 +21,15 @@ cudaError_t level_occupancy_a(int L, bool finest, int src_kind, int* out) {
     }
 }
 
+cudaError_t level_stream_occupancy_a(int L, int src_kind, int* out) {
+    switch (L) {
+        case 4: return level_stream_blocks_per_sm<4>(src_kind, out);
+        case 8: return level_stream_blocks_per_sm<8>(src_kind, out);
+        case 16: return level_stream_blocks_per_sm<16>(src_kind, out);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 cudaError_t upload_twiddles_level_a() { return upload_twiddles(); }
 
 }  // namespace omni

@@ -19,6 +19,14 @@ cudaError_t level_occupancy_b(int L, bool finest, int src_kind, int* out) {
     }
 }
 
+cudaError_t level_stream_occupancy_b(int L, int src_kind, int* out) {
+    switch (L) {
+        case 32: return level_stream_blocks_per_sm<32>(src_kind, out);
+        case 64: return level_stream_blocks_per_sm<64>(src_kind, out);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 cudaError_t upload_twiddles_level_b() { return upload_twiddles(); }
 
 }  // namespace omni

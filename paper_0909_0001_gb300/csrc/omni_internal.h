@@ -48,6 +48,7 @@ struct Pass {
     int q_shift;    // inverse: output q holds lag q - q_shift, i.e. bin (q - q_shift) mod L
     int L1, L2;     // KIND_SMEM split
     int W;          // KIND_SMEM / KIND_LEVEL: consecutive inner indices per unit
+    int grid_cap;   // KIND_LEVEL finest MID: CTAs of the persistent kernel (0 = not used)
     int64_t inner, outer;
     const float2* tw;  // KIND_DIRECT: w_L^m = exp(-2 pi i m / L), m < L
 };
@@ -79,6 +80,9 @@ cudaError_t launch_pass(const Pass& p, const PassArgs& a, cudaStream_t stream);
 
 // Resident CTAs per SM of the LAST-mode kernel of a KIND_LEVEL pass.
 cudaError_t level_last_occupancy(const Pass& p, int src_kind, int* blocks_per_sm);
+
+// Resident CTAs per SM of the persistent finest-level MID kernel.
+cudaError_t level_stream_occupancy(const Pass& p, int src_kind, int* blocks_per_sm);
 
 // Set the calling thread's omni_last_error() message.
 void set_last_error(const char* msg);
