@@ -262,6 +262,32 @@ omni_status build_passes(omni_plan* pl) {
     }
     pl->fwd.clear();
     pl->fwd_elems = 0;
+    if (pl->precision == OMNI_MIXED_FP16) {
+        // tensor-core stages: level 1 (16x16 -> 32x32 per block), level 2 (8x8 -> 16x16) + |F|^2
+        stages.clear();
+        Pass pa{};
+        pa.axis = 0;
+        pa.kind = KIND_TC_A;
+        pa.mode = MODE_MID;
+        pa.L = g.Lp[0];
+        pa.n = g.n[0];
+        pa.q_out = g.Lp[0] * g.Lp[1];
+        pa.inner = 1;
+        pa.outer = (int64_t)g.n[2] * g.n[3];
+        Pass pb{};
+        pb.axis = 2;
+        pb.kind = KIND_TC_B;
+        pb.mode = MODE_LAST;
+        pb.L = g.Lp[2];
+        pb.n = g.n[2];
+        pb.q_out = g.Lp[2] * g.Lp[3];
+        pb.inner = (int64_t)g.Lp[0] * g.Lp[1];
+        pb.outer = 1;
+        pb.W = 32;
+        pl->fwd.push_back(pa);
+        pl->fwd.push_back(pb);
+        pl->fwd_elems = pa.outer * pa.q_out;
+    }
     for (size_t k = 0; k < stages.size(); ++k) {
         const int d = stages[k].first;
         const bool level = stages[k].second;
@@ -337,6 +363,7 @@ void choose_chunks(omni_plan* pl) {
     int64_t ctas = 1;
     switch (last.kind) {
         case KIND_LEVEL:
+        case KIND_TC_B:
         case KIND_SMEM: ctas = (last.inner + last.W - 1) / last.W; break;
         case KIND_REG: ctas = (last.inner + 255) / 256; break;
         default: ctas = (last.L * last.inner + 255) / 256; break;
@@ -346,6 +373,7 @@ void choose_chunks(omni_plan* pl) {
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, pl->device) != cudaSuccess) sms = 0;
     const int first_src = pl->fwd.size() == 1 ? (pl->dtype == OMNI_IN_CI8 ? SRC_CI8 : SRC_CF32) : SRC_BUF;
     if (last.kind == KIND_LEVEL && level_last_occupancy(last, first_src, &per_sm) != cudaSuccess) per_sm = 0;
+    if (last.kind == KIND_TC_B && tc_occupancy(KIND_TC_B, &per_sm) != cudaSuccess) per_sm = 0;
     cudaGetLastError();
     int64_t slots = (int64_t)std::max(sms, 1) * std::max(per_sm, 2);
     if (sms <= 0) slots = 304;
@@ -382,7 +410,8 @@ void release(omni_plan* pl) {
 }
 
 const char* kind_name(int k) {
-    return k == KIND_REG ? "reg" : k == KIND_SMEM ? "smem" : k == KIND_LEVEL ? "level" : "direct";
+    return k == KIND_REG ? "reg" : k == KIND_SMEM ? "smem" : k == KIND_LEVEL ? "level"
+         : k == KIND_TC_A || k == KIND_TC_B ? "tc" : "direct";
 }
 const char* mode_name(int m) {
     return m == MODE_MID ? "mid" : m == MODE_LAST ? "last" : m == MODE_INV_MID ? "mid" : "last";
@@ -393,7 +422,7 @@ void init_stats(omni_plan* pl) {
     for (int inv = 0; inv < 2; ++inv)
         for (const Pass& p : inv ? pl->inv : pl->fwd) {
             omni_kernel_stat st{};
-            if (p.kind == KIND_LEVEL)
+            if (p.kind == KIND_LEVEL || p.kind == KIND_TC_A || p.kind == KIND_TC_B)
                 snprintf(st.name, sizeof st.name, "%s axis%d+%d %s%d %s", inv ? "inv" : "fwd", p.axis,
                          p.axis + 1, kind_name(p.kind), p.L, mode_name(p.mode));
             else
@@ -422,7 +451,8 @@ double src_bytes(int src_kind) {
 // Algorithmic bytes of one launch: inputs read plus outputs written.
 double pass_bytes(const Pass& p, const PassArgs& a) {
     const double in = src_bytes(a.src_kind);
-    const double n_in = p.kind == KIND_LEVEL ? (double)p.n * p.n : (double)p.n;
+    const bool two_axes = p.kind == KIND_LEVEL || p.kind == KIND_TC_A || p.kind == KIND_TC_B;
+    const double n_in = two_axes ? (double)p.n * p.n : (double)p.n;
     switch (p.mode) {
         case MODE_MID:
             return (double)a.S * p.outer * p.inner * (n_in * in + p.q_out * 8.0);
@@ -594,9 +624,11 @@ omni_status omni_plan_create(const omni_level* levels, int n_levels, int64_t n_c
         delete pl;
         return st;
     }
-    if (precision == OMNI_MIXED_FP16) {
+    if (precision == OMNI_MIXED_FP16 && !tc_supports(pl->g.n, pl->g.D, dtype == OMNI_IN_CI8)) {
         delete pl;
-        return fail(OMNI_ERR_UNSUPPORTED, "the mixed-precision path is not available for this hierarchy");
+        return fail(OMNI_ERR_UNSUPPORTED,
+                    "the mixed-precision path supports int8 voltages on a 2-level hierarchy of "
+                    "16x16 blocks on an 8x8 grid");
     }
     pl->C = n_channels;
     pl->dtype = dtype;
@@ -620,6 +652,14 @@ omni_status omni_plan_create(const omni_level* levels, int n_levels, int64_t n_c
     // persistent finest-level passes: one wave of resident CTAs
     for (size_t k = 0; k < pl->fwd.size(); ++k) {
         Pass& p = pl->fwd[k];
+        if (p.kind == KIND_TC_A) {
+            int per_sm = 0, sms = 0;
+            if (tc_occupancy(KIND_TC_A, &per_sm) == cudaSuccess &&
+                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, pl->device) == cudaSuccess)
+                p.grid_cap = per_sm * sms;
+            cudaGetLastError();
+            continue;
+        }
         if (p.kind != KIND_LEVEL || p.mode != MODE_MID || p.inner != 1) continue;
         const int src = k == 0 ? (pl->dtype == OMNI_IN_CI8 ? SRC_CI8 : SRC_CF32) : SRC_BUF;
         int per_sm = 0, sms = 0;

@@ -34,6 +34,8 @@ cudaError_t launch_pass(const Pass& p, const PassArgs& a, cudaStream_t st) {
             return p.L <= 512 ? launch_smem_a(p, a, st)
                  : p.L <= 2048 ? launch_smem_b(p, a, st) : launch_smem_c(p, a, st);
         case KIND_LEVEL: return p.L <= 16 ? launch_level_a(p, a, st) : launch_level_b(p, a, st);
+        case KIND_TC_A:
+        case KIND_TC_B: return launch_tc(p, a, st);
         default: return launch_direct(p, a, st);
     }
 }
@@ -61,6 +63,7 @@ cudaError_t init_device_tables() {
                     upload_twiddles_smem_b, upload_twiddles_smem_c, upload_twiddles_level_a,
                     upload_twiddles_level_b})
         if ((e = up()) != cudaSuccess) return e;
+    if ((e = upload_tc_tables()) != cudaSuccess) return e;
     done.push_back(dev);
     return cudaSuccess;
 }

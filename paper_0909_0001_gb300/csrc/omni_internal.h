@@ -30,7 +30,9 @@ enum PassKind : int {
     KIND_REG = 0,    // whole line in one thread's registers (power of two <= 64)
     KIND_SMEM = 1,   // four-step L = L1 * L2 through shared memory (power of two <= 4096)
     KIND_DIRECT = 2, // direct DFT from a twiddle table (any length)
-    KIND_LEVEL = 3   // both axes of one square level (L_a = L_b <= 64) in shared memory
+    KIND_LEVEL = 3,  // both axes of one square level (L_a = L_b <= 64) in shared memory
+    KIND_TC_A = 4,   // mixed precision, finest level as split-FP16 tensor-core GEMMs
+    KIND_TC_B = 5    // mixed precision, coarse level + |F|^2 as tensor-core GEMMs (LAST)
 };
 
 // One axis transform.  The data of one sample (or channel) is viewed as
@@ -83,6 +85,12 @@ cudaError_t level_last_occupancy(const Pass& p, int src_kind, int* blocks_per_sm
 
 // Resident CTAs per SM of the persistent finest-level MID kernel.
 cudaError_t level_stream_occupancy(const Pass& p, int src_kind, int* blocks_per_sm);
+
+// Mixed-precision (tensor-core) path: supported lattices, tables, launches.
+bool tc_supports(const int32_t* n, int D, int dtype_is_ci8);
+cudaError_t upload_tc_tables();
+cudaError_t tc_occupancy(int kind, int* blocks_per_sm);
+cudaError_t launch_tc(const Pass& p, const PassArgs& a, cudaStream_t stream);
 
 // Set the calling thread's omni_last_error() message.
 void set_last_error(const char* msg);

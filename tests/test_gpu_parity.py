@@ -19,10 +19,10 @@ pytestmark = pytest.mark.gpu
 TOL_FP32 = 1e-5
 
 
-def gpu_vis(levels, x, dtype="cf32", calls=None):
+def gpu_vis(levels, x, dtype="cf32", calls=None, precision="fp32"):
     """Visibilities [C][Q] from the CUDA library for voltages x [C][T][N][2]."""
     C = x.shape[0]
-    with omni.Plan(levels, C, dtype=dtype) as plan:
+    with omni.Plan(levels, C, dtype=dtype, precision=precision) as plan:
         xd = x.cuda()
         if calls is None:
             plan.correlate(xd)
@@ -40,8 +40,8 @@ def relerr_per_channel(V, ref):
     return float(np.max(num / den))
 
 
-def check(levels, x, dtype="cf32", tol=TOL_FP32):
-    V = gpu_vis(levels, x, dtype)
+def check(levels, x, dtype="cf32", tol=TOL_FP32, precision="fp32"):
+    V = gpu_vis(levels, x, dtype, precision=precision)
     ref = oracle.correlate(synth.lattice_dims(levels), x)
     err = relerr_per_channel(V, ref)
     assert err <= tol, f"relative Frobenius error {err:.3e} > {tol:g}"
@@ -248,3 +248,58 @@ def test_level_and_per_axis_paths_agree(monkeypatch):
     monkeypatch.setenv("OMNI_LEVEL_PASSES", "0")
     per_axis = gpu_vis(w.levels, x, dtype="ci8")
     assert relerr_per_channel(fused, per_axis) <= 2e-6
+
+
+# ---------------------------------------------------------------- mixed precision
+
+TOL_MIXED = 1e-4
+
+
+def test_mixed_matches_oracle_ragged():
+    w = synth.workload("hier2")
+    x = synth.voltages(w, channels=3, samples=7)
+    V, _ = check(w.levels, x, dtype="ci8", tol=TOL_MIXED, precision="mixed")
+    fp32 = gpu_vis(w.levels, x, dtype="ci8")
+    assert relerr_per_channel(V, fp32) <= TOL_MIXED
+
+
+def test_mixed_extreme_int8_values():
+    """Full-scale +-127 voltages: the FP16 operands must stay in range."""
+    w = synth.workload("hier2")
+    x = synth.random_complex(w.dims, 2, 3, seed=31, dtype="ci8", sigma=400.0)  # clipped to +-127
+    assert int(x.abs().max()) == 127
+    check(w.levels, x, dtype="ci8", tol=TOL_MIXED, precision="mixed")
+    ones = torch.full_like(x, 127)
+    check(w.levels, ones, dtype="ci8", tol=TOL_MIXED, precision="mixed")
+
+
+def test_mixed_all_ones_exact_after_rounding():
+    w = synth.workload("hier2")
+    V = gpu_vis(w.levels, synth.all_ones(w.dims, 1, 2, dtype="ci8"), dtype="ci8", precision="mixed")
+    _, red, _ = omni.baselines(w.levels)
+    np.testing.assert_array_equal(np.rint(V.real[0]).astype(np.int64), 2 * red)
+
+
+def test_mixed_full_size_sampled():
+    w = synth.workload("hier2")
+    xd = synth.voltages(w, device="cuda")
+    with omni.Plan(w.levels, w.channels, dtype=w.dtype, precision="mixed") as plan:
+        plan.correlate(xd)
+        V = plan.visibilities().cpu().numpy()
+    x = xd.cpu()
+    del xd
+    rng = np.random.default_rng(6)
+    chans = np.repeat(np.array([1, 30, 62]), 96)
+    lags = rng.integers(0, V.shape[1], chans.size)
+    lags[::96] = V.shape[1] // 2
+    err, _, _ = sampled_error(w.levels, x, V, chans, lags)
+    assert err <= TOL_MIXED, err
+    property_checks(w.levels, x, V, tol=TOL_MIXED)
+
+
+def test_mixed_rejects_unsupported_shapes():
+    with pytest.raises(omni.OmniError) as e:
+        omni.Plan(synth.workload("hier2").levels, 1, dtype="cf32", precision="mixed")
+    assert e.value.status == 3
+    with pytest.raises(omni.OmniError):
+        omni.Plan([synth.Level(16, 16)], 1, dtype="ci8", precision="mixed")
