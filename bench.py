@@ -4,7 +4,9 @@
 One step = one pass of the whole hot path over one batch of synthetic input:
 omni_correlate over C channels x T samples (scatter, forward 2n-D FFT, |F|^2
 time integration) followed by omni_visibilities (inverse 2n-D FFT, 1/L,
-lag gather) with the accumulator reset.  Metric: antenna-samples per second
+lag gather) with the accumulator reset.  The headline path is the mixed
+precision one (split-FP16 tensor-core DFT-GEMMs); the plain FP32 FFT path is
+timed beside it ("fp32_path").  Metric: antenna-samples per second
 (N x T x C per step).  The default workload is the 2-level 16x16 / 8x8
 hierarchy (N = 16384, 64 channels x 1024 samples of int8 voltages, 2.1 GB per
 step, larger than L2, so no flush is needed between steps).
@@ -42,7 +44,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="hier2")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp32", "mixed"],
+                    help="headline path; the other one is timed beside it")
+    ap.add_argument("--no-compare", action="store_true", help="skip the FP32 comparison run")
     ap.add_argument("--channels", type=int, default=None,
                     help="run a smaller case of the workload (profiling)")
     ap.add_argument("--samples", type=int, default=None,
@@ -50,11 +54,6 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
-
-
-def dist_env():
-    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
-            int(os.environ.get("WORLD_SIZE", 1)))
 
 
 def workload_config(w, precision):
@@ -136,15 +135,6 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ roofline
 
-def measured_peaks():
-    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(p):
-        with open(p) as f:
-            d = json.load(f)
-        return d.get("hbm_gbs"), "measured"
-    return 6800.0, "fallback"
-
-
 def kernel_source_hash():
     from paper_0909_0001_gb300.build import CSRC
     h = hashlib.sha256()
@@ -155,7 +145,7 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel_name, workload):
+def recorded_traffic(kernel_name, workload, precision):
     """DRAM bytes per launch from a committed ncu summary, if it matches this build."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
@@ -164,31 +154,58 @@ def recorded_traffic(kernel_name, workload):
     with open(path) as f:
         for line in f:
             p = line.strip().split("|")
-            if len(p) >= 4 and p[0].strip() == workload and p[1].strip() == kernel_name \
-                    and p[2].strip() == want:
+            if len(p) >= 5 and p[0].strip() == workload and p[1].strip() == precision \
+                    and p[2].strip() == kernel_name and p[3].strip() == want:
                 try:
-                    return float(p[3])
+                    return float(p[4])
                 except ValueError:
                     return None
     return None
 
 
-def roofline(stats, workload):
+def alu_peak_tflops(sm_mhz):
+    """FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x clock."""
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def roofline(stats, workload, path_precision):
+    """Roofline of the dominant kernel (largest share of the event-timed region)."""
     timed = [s for s in stats if s["launches"] > 0 and s["total_ms"] > 0]
     if not timed:
         return None
     top = max(timed, key=lambda s: s["total_ms"])
-    peak, kind = measured_peaks()
-    avg_ms = top["total_ms"] / top["launches"]
+    peaks = {}
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            peaks = json.load(f)
+    kind = "measured" if peaks else "fallback"
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    # the kernel runs inside a long step: sustained tensor peak; fp16 dense = bf16 dense
+    tensor_peak = peaks.get("bf16_tflops_sustained", 1700.0)
+    alu_peak = alu_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
+    avg_s = top["total_ms"] / top["launches"] * 1e-3
     bytes_per_launch = top["bytes"] / top["launches"]
-    achieved = bytes_per_launch / (avg_ms * 1e-3) / 1e9
-    traffic = recorded_traffic(top["name"], workload)
+    flops_per_launch = top["flops"] / top["launches"]
+    gbs = bytes_per_launch / avg_s / 1e9
+    tfs = flops_per_launch / avg_s / 1e12
     total = sum(s["total_ms"] for s in timed)
-    return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "traffic": traffic,
-            "kernel": top["name"], "peak_kind": kind,
-            "bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_ms,
-            "share_of_kernel_time": round(top["total_ms"] / total, 4)}
+    hbm = {"achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+           "frac": round(gbs / hbm_peak, 4), "bytes_per_launch": bytes_per_launch}
+    if top["tensor"]:
+        main = {"bound": "tensor", "achieved": round(tfs, 2), "peak": tensor_peak,
+                "unit": "TFLOP/s", "frac": round(tfs / tensor_peak, 4),
+                "peak_note": "bf16_tflops_sustained of %s (fp16 dense = bf16 dense)" % kind}
+    else:
+        main = {"bound": "alu", "achieved": round(tfs, 2), "peak": round(alu_peak, 1),
+                "unit": "TFLOP/s", "frac": round(tfs / alu_peak, 4),
+                "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 x max SM clock"}
+    main.update({"traffic": recorded_traffic(top["name"], workload, path_precision),
+                 "kernel": top["name"], "flops_per_launch": flops_per_launch,
+                 "avg_launch_ms": avg_s * 1e3,
+                 "share_of_kernel_time": round(top["total_ms"] / total, 4),
+                 "hbm": hbm})
+    return main
 
 
 # ------------------------------------------------------------------ CPU oracle
@@ -219,7 +236,8 @@ def oracle_rate(w, x_host, target_s=15.0, max_samples=64):
 # ------------------------------------------------------------------ arms
 
 def run_reference(args):
-    rank, _, world = dist_env()
+    from paper_0909_0001_gb300.multirank import rank_env
+    rank, _, world = rank_env()
     if rank != 0:
         return
     from paper_0909_0001_gb300 import synth
@@ -246,15 +264,43 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def timed_steps(plan, x, vis, steps, warmup, stream, barrier, profile):
+    """Warm up, then time `steps` steps (correlate + visibilities) with CUDA events."""
+    import torch
+
+    def step():
+        plan.correlate(x)
+        plan.visibilities(reset=True, out=vis)
+
+    for _ in range(max(3, warmup)):
+        step()
+    torch.cuda.synchronize()
+    plan.kernel_stats(clear=True)
+    plan.profile(profile)
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    plan.profile(False)
+    return e0.elapsed_time(e1) / steps, plan.kernel_stats(clear=True)
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
-    from paper_0909_0001_gb300 import omni, synth
+    from paper_0909_0001_gb300 import multirank, omni, synth
 
-    rank, local_rank, world = dist_env()
+    rank, local_rank, world = multirank.rank_env()
     torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
     if world > 1:
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+        dist.init_process_group("nccl", device_id=dev)
 
     def barrier():
         if world > 1:
@@ -266,41 +312,26 @@ def run_ours(args):
     if args.samples:
         w.samples = args.samples
     units = w.n_antennas * w.samples * w.channels
-    x = synth.voltages(w, device="cuda", seed=w.seed + 7919 * rank)
-    plan = omni.Plan(w.levels, w.channels, dtype=w.dtype, precision=args.precision)
-    vis = torch.empty((w.channels, plan.n_lags), dtype=torch.complex128, device="cuda")
+    # weak scaling: every rank correlates its own channels (no data-path collective)
+    x = synth.voltages(w, device="cuda", channel_offset=rank * w.channels)
     stream = torch.cuda.current_stream()
-
-    def step():
-        plan.correlate(x)
-        plan.visibilities(reset=True, out=vis)
-
-    for _ in range(max(3, args.warmup)):
-        step()
-    torch.cuda.synchronize()
-    plan.kernel_stats(clear=True)
-    plan.profile(True)
-
-    barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(torch.cuda.current_device()) as clk:
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.steps):
-            step()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        barrier()
-    plan.profile(False)
-    ms = e0.elapsed_time(e1) / args.steps
-    stats = plan.kernel_stats(clear=True)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * units / (ms * 1e-3)
-    launches = sum(s["launches"] for s in stats)
+    results = {}
+    precisions = [args.precision] + ([] if args.precision == "fp32" or args.no_compare else ["fp32"])
+    for prec in precisions:
+        plan = omni.Plan(w.levels, w.channels, dtype=w.dtype, precision=prec)
+        vis = torch.empty((w.channels, plan.n_lags), dtype=torch.complex128, device="cuda")
+        # both paths are timed the same way: per-pass CUDA events on, clocks sampled
+        with ClockSampler(torch.cuda.current_device()) as clk:
+            ms, stats = timed_steps(plan, x, vis, args.steps, args.warmup, stream, barrier, True)
+        if prec == args.precision:
+            clocks = clk.summary()
+        rate, slowest = multirank.job_rate(units, ms * 1e-3, device=dev)
+        results[prec] = {"plan": plan, "vis": vis, "ms": slowest * 1e3, "value": rate,
+                         "stats": stats}
+        if prec != args.precision:
+            plan.close()
+    head = results[args.precision]
+    plan, vis = head["plan"], head["vis"]
 
     # end to end through the host-buffer entry points
     e2e = None
@@ -318,14 +349,11 @@ def run_ours(args):
             plan.visibilities_host(reset=True, out=vh)
         torch.cuda.synchronize()
         dt = (time.perf_counter() - t0) / n_e2e
-        if world > 1:
-            t = torch.tensor([dt], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
-        e2e = {"value": world * units / dt, "unit": UNIT,
+        e2e_rate, e2e_s = multirank.job_rate(units, dt, device=dev)
+        e2e = {"value": e2e_rate, "unit": UNIT,
                "h2d_bytes_per_step": xh.numel() * xh.element_size(),
                "d2h_bytes_per_step": vh.numel() * vh.element_size(),
-               "ms_per_step": dt * 1e3, "steps": n_e2e}
+               "ms_per_step": e2e_s * 1e3, "steps": n_e2e}
         del xh, vh
 
     cpu = None
@@ -334,17 +362,25 @@ def run_ours(args):
         cpu = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
 
     if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-                "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms,
+        stats = head["stats"]
+        line = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": head["ms"],
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f32", "data": "synthetic",
+                "dtype": "f16x3+f32" if args.precision == "mixed" else "f32",
+                "data": "synthetic",
                 "config": dict(workload_config(w, args.precision),
-                               parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
-                "roofline": roofline(stats, args.workload),
-                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk.summary(),
+                               parallelism=f"{world} ranks x {w.channels} channels"
+                               if world > 1 else "single GPU"),
+                "roofline": roofline(stats, args.workload, args.precision),
+                "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": sum(s["launches"] for s in stats),
+                "clocks": clocks,
                 "kernels": [{k: s[k] for k in ("name", "launches", "total_ms")}
                             for s in stats if s["launches"]]}
+        if "fp32" in results and args.precision != "fp32":
+            f = results["fp32"]
+            line["fp32_path"] = {"value": f["value"], "ms_per_step": f["ms"],
+                                 "speedup_of_headline": head["value"] / f["value"]}
         print(json.dumps(line), flush=True)
     plan.close()
     if world > 1:

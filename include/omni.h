@@ -148,6 +148,11 @@ typedef struct omni_kernel_stat {
                           launch on the launching stream (0 unless profiling) */
     double bytes;      /* algorithmic bytes of all launches: inputs read plus
                           outputs written at their stored precision */
+    double flops;      /* algorithmic floating-point operations of all launches:
+                          5 L log2 L per L-point line transform plus 3 per |F|^2
+                          term for the FFT passes; the executed m16n8k16 products
+                          (4096 each) for the tensor-core passes */
+    int32_t tensor;    /* 1 when the pass runs on tensor cores */
 } omni_kernel_stat;
 
 /* Start (enable != 0) or stop recording a CUDA event pair around every kernel

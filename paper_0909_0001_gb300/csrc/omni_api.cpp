@@ -428,6 +428,7 @@ void init_stats(omni_plan* pl) {
             else
                 snprintf(st.name, sizeof st.name, "%s axis%d %s%d %s", inv ? "inv" : "fwd", p.axis,
                          kind_name(p.kind), p.L, mode_name(p.mode));
+            st.tensor = (p.kind == KIND_TC_A || p.kind == KIND_TC_B) ? 1 : 0;
             pl->stats.push_back(st);
         }
 }
@@ -465,12 +466,38 @@ double pass_bytes(const Pass& p, const PassArgs& a) {
     }
 }
 
+// Algorithmic flops of one launch (see omni_kernel_stat).
+double pass_flops(const Pass& p, const PassArgs& a) {
+    const double lg = std::log2((double)std::max(p.L, 2));
+    const double line = 5.0 * p.L * lg;
+    switch (p.kind) {
+        case KIND_TC_A:  // per 16x16 block: 32 + 96 products
+            return (double)a.S * p.outer * 128.0 * 4096.0;
+        case KIND_TC_B:  // per level-1 frequency and sample: 6 + 12 products, |F|^2
+            return (double)a.S * a.tc * p.inner * (18.0 * 4096.0 + 3.0 * p.q_out);
+        case KIND_LEVEL: {
+            const double per_unit = (double)p.n * line + (double)p.L * line;  // axis a, axis b
+            if (p.mode == MODE_LAST)
+                return (double)a.S * a.tc * p.inner * (per_unit + 3.0 * p.q_out);
+            return (double)a.S * p.outer * p.inner * per_unit;
+        }
+        default: {
+            const double lines = (p.mode == MODE_LAST) ? (double)a.S * a.tc * p.inner
+                                                       : (double)a.S * p.outer * p.inner;
+            const double extra = (p.mode == MODE_LAST) ? 3.0 * p.L : 0.0;
+            const double per = p.kind == KIND_DIRECT ? 8.0 * p.n * p.q_out : line;
+            return lines * (per + extra);
+        }
+    }
+}
+
 // Launch pass number idx (index into stats) with optional event timing.
 cudaError_t launch_counted(omni_plan* pl, int idx, const Pass& p, const PassArgs& a,
                            cudaStream_t st) {
     omni_kernel_stat& s = pl->stats[idx];
     s.launches += 1;
     s.bytes += pass_bytes(p, a);
+    s.flops += pass_flops(p, a);
     if (!pl->profiling) return launch_pass(p, a, st);
     cudaEvent_t e0 = pool_event(pl), e1 = pool_event(pl);
     if (!e0 || !e1) return cudaErrorMemoryAllocation;
@@ -852,6 +879,7 @@ omni_status omni_profile_read(omni_plan* pl, omni_kernel_stat* out, int max, int
             s.launches = 0;
             s.total_ms = 0.0;
             s.bytes = 0.0;
+            s.flops = 0.0;
         }
     return OMNI_OK;
 }

@@ -53,7 +53,9 @@ constexpr int kTileKA = 32;               // level-1 frequencies per stage-B CTA
 constexpr int kPitchB = 65;               // shared row pitch (blocks) per kA, odd
 
 __device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-    asm volatile(
+    // not volatile: the product has no side effects, so the compiler may
+    // interleave independent accumulators
+    asm(
         "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 "
         "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
         : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
@@ -104,24 +106,29 @@ __global__ void __launch_bounds__(kStageAWarps * 32) tc_stage_a(Pass p, PassArgs
             ci8_pair(*reinterpret_cast<const uint32_t*>(row + 4 * t), bre[nt][0], bim[nt][0]);
             ci8_pair(*reinterpret_cast<const uint32_t*>(row + 4 * t + 16), bre[nt][1], bim[nt][1]);
         }
-        // GEMM 1 (X exact: twiddle hi and lo terms)
+        // GEMM 1 (X exact: twiddle hi and lo terms); the 8 accumulators are
+        // updated round-robin so that consecutive products are independent
         float d0[4][2][4];
 #pragma unroll
         for (int mt = 0; mt < 4; ++mt)
 #pragma unroll
-            for (int nt = 0; nt < 2; ++nt) {
+            for (int nt = 0; nt < 2; ++nt)
 #pragma unroll
                 for (int r = 0; r < 4; ++r) d0[mt][nt][r] = 0.f;
 #pragma unroll
-                for (int ks = 0; ks < 2; ++ks)
+        for (int ks = 0; ks < 2; ++ks)
 #pragma unroll
-                    for (int hl = 0; hl < 2; ++hl) {
-                        const uint4 w = sA1[mt][ks][hl][lane];
-                        const uint32_t af[4] = {w.x, w.y, w.z, w.w};
+            for (int hl = 0; hl < 2; ++hl)
+#pragma unroll
+                for (int mt = 0; mt < 4; ++mt) {
+                    const uint4 w = sA1[mt][ks][hl][lane];
+                    const uint32_t af[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                    for (int nt = 0; nt < 2; ++nt) {
                         if (ks == 0) mma16816(d0[mt][nt], af, bre[nt][0], bre[nt][1]);
                         else mma16816(d0[mt][nt], af, bim[nt][0], bim[nt][1]);
                     }
-            }
+                }
         // chain: A operand of GEMM 2, [mt'][ks'] from D0 rows (ks' = 0: re, 1: im)
         uint32_t ah[2][2][4], al[2][2][4];
 #pragma unroll
@@ -147,15 +154,16 @@ __global__ void __launch_bounds__(kStageAWarps * 32) tc_stage_a(Pass p, PassArgs
             for (int kp = 0; kp < 2; ++kp) {
                 const uint2 bhr = sB2[kp][nt][0][lane], blr = sB2[kp][nt][1][lane];
                 const uint2 bhi = sB2[kp][nt + 4][0][lane], bli = sB2[kp][nt + 4][1][lane];
+                // term-major: the four accumulators (re/im x mp) are independent
 #pragma unroll
-                for (int mp = 0; mp < 2; ++mp) {
-                    mma16816(dre[mp], ah[mp][kp], bhr.x, bhr.y);
-                    mma16816(dre[mp], ah[mp][kp], blr.x, blr.y);
-                    mma16816(dre[mp], al[mp][kp], bhr.x, bhr.y);
-                    mma16816(dim[mp], ah[mp][kp], bhi.x, bhi.y);
-                    mma16816(dim[mp], ah[mp][kp], bli.x, bli.y);
-                    mma16816(dim[mp], al[mp][kp], bhi.x, bhi.y);
-                }
+                for (int term = 0; term < 3; ++term)
+#pragma unroll
+                    for (int mp = 0; mp < 2; ++mp) {
+                        const uint32_t(&aa)[4] = term == 2 ? al[mp][kp] : ah[mp][kp];
+                        const uint2 br = term == 1 ? blr : bhr, bi = term == 1 ? bli : bhi;
+                        mma16816(dre[mp], aa, br.x, br.y);
+                        mma16816(dim[mp], aa, bi.x, bi.y);
+                    }
             }
             // Y[k2][k1]: k1 = 16 mp + g (+8), k2 = 8 nt + 2t (+1)
 #pragma unroll
@@ -244,13 +252,14 @@ __global__ void __launch_bounds__(kStageBWarps * 32, 2) tc_stage_b(Pass p, PassA
             split2(z0.y, z1.y, bh1, bl1);  // rows im m3
             float d2[2][4];
 #pragma unroll
-            for (int mt = 0; mt < 2; ++mt) {
+            for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
                 for (int r = 0; r < 4; ++r) d2[mt][r] = 0.f;
-                mma16816(d2[mt], a3[mt][0], bh0, bh1);
-                mma16816(d2[mt], a3[mt][1], bh0, bh1);
-                mma16816(d2[mt], a3[mt][0], bl0, bl1);
-            }
+#pragma unroll
+            for (int term = 0; term < 3; ++term)
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt)
+                    mma16816(d2[mt], a3[mt][term == 1 ? 1 : 0], term == 2 ? bl0 : bh0, term == 2 ? bl1 : bh1);
             uint32_t ah[4], al[4];
             split2(d2[0][0], d2[0][1], ah[0], al[0]);
             split2(d2[0][2], d2[0][3], ah[1], al[1]);
@@ -258,13 +267,14 @@ __global__ void __launch_bounds__(kStageBWarps * 32, 2) tc_stage_b(Pass p, PassA
             split2(d2[1][2], d2[1][3], ah[3], al[3]);
             float d3[4][4];
 #pragma unroll
-            for (int nt = 0; nt < 4; ++nt) {
+            for (int nt = 0; nt < 4; ++nt)
 #pragma unroll
                 for (int r = 0; r < 4; ++r) d3[nt][r] = 0.f;
-                mma16816(d3[nt], ah, b4[nt][0][0], b4[nt][0][1]);
-                mma16816(d3[nt], ah, b4[nt][1][0], b4[nt][1][1]);
-                mma16816(d3[nt], al, b4[nt][0][0], b4[nt][0][1]);
-            }
+#pragma unroll
+            for (int term = 0; term < 3; ++term)
+#pragma unroll
+                for (int nt = 0; nt < 4; ++nt)
+                    mma16816(d3[nt], term == 2 ? al : ah, b4[nt][term == 1 ? 1 : 0][0], b4[nt][term == 1 ? 1 : 0][1]);
 #pragma unroll
             for (int nt = 0; nt < 2; ++nt)
 #pragma unroll

@@ -47,7 +47,8 @@ class omni_level(ctypes.Structure):
 
 class omni_kernel_stat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 64), ("launches", ctypes.c_int64),
-                ("total_ms", ctypes.c_double), ("bytes", ctypes.c_double)]
+                ("total_ms", ctypes.c_double), ("bytes", ctypes.c_double),
+                ("flops", ctypes.c_double), ("tensor", ctypes.c_int32)]
 
 
 _lib: Optional[ctypes.CDLL] = None
@@ -237,13 +238,14 @@ class Plan:
         _check(load().omni_profile_enable(self._h, int(enable)))
 
     def kernel_stats(self, clear: bool = False) -> list:
-        """Per-pass [{name, launches, total_ms, bytes}] (waits for recorded events)."""
+        """Per-pass [{name, launches, total_ms, bytes, flops, tensor}] (waits for recorded events)."""
         n = ctypes.c_int()
         _check(load().omni_profile_read(self._h, None, 0, ctypes.byref(n), 0))
         arr = (omni_kernel_stat * max(1, n.value))()
         _check(load().omni_profile_read(self._h, arr, n.value, ctypes.byref(n), int(clear)))
         return [{"name": arr[i].name.decode(), "launches": arr[i].launches,
-                 "total_ms": arr[i].total_ms, "bytes": arr[i].bytes} for i in range(n.value)]
+                 "total_ms": arr[i].total_ms, "bytes": arr[i].bytes, "flops": arr[i].flops,
+                 "tensor": bool(arr[i].tensor)} for i in range(n.value)]
 
     def reset(self, stream=None) -> None:
         _check(load().omni_reset(self._h, _stream_ptr(stream)))
