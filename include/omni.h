@@ -101,6 +101,28 @@ omni_status omni_baselines(const omni_level* levels, int n_levels, int32_t* dm,
 omni_status omni_plan_create(const omni_level* levels, int n_levels, int64_t n_channels,
                              omni_dtype dtype, omni_precision precision, omni_plan** out);
 
+/* A plan for n_arrays independent arrays of possibly different hierarchies
+ * (Sec. III: several separate omniscopes, each correlated on its own), all with
+ * n_channels channels of the same dtype.  levels_per_array[a] has
+ * n_levels_per_array[a] levels.  Runs of consecutive arrays with the same level
+ * shapes are correlated together, one launch per transform pass for the whole
+ * run, so ordering the arrays by shape gives the fewest launches.
+ * The same omni_correlate*, omni_visibilities*, omni_reset, omni_sync,
+ * omni_profile_* and omni_plan_destroy calls apply:
+ *   voltages: the arrays' [C][T][N_a] blocks concatenated in array order;
+ *   visibilities: the arrays' [C][n_lags_a] complex128 blocks concatenated.
+ * omni_plan_info on a batch plan reports n_dims = 0, n_antennas = sum N_a and
+ * n_lags = sum n_lags_a; omni_batch_info gives the per-array sizes. */
+omni_status omni_plan_create_batch(const omni_level* const* levels_per_array,
+                                   const int* n_levels_per_array, int n_arrays,
+                                   int64_t n_channels, omni_dtype dtype,
+                                   omni_precision precision, omni_plan** out);
+
+/* Per-array sizes of a batch plan (n_arrays = 1 for a single-array plan):
+ * antennas[a] = N_a, lags[a] = n_lags_a (arrays may be NULL to query n_arrays). */
+omni_status omni_batch_info(const omni_plan* plan, int* n_arrays, int64_t* antennas,
+                            int64_t* lags);
+
 /* Free everything the plan owns (synchronises its device work first). */
 void omni_plan_destroy(omni_plan* plan);
 
@@ -112,8 +134,9 @@ omni_status omni_plan_info(const omni_plan* plan, int* n_dims, int32_t* dims,
 
 /* Accumulate T samples of every channel (Sec. II.C: FFT, |.|^2, summed over
  * time; Appendix A steps 3-5).  volts_dev: DEVICE pointer to [C][T][N]
- * complex voltages of the plan's dtype, 16-byte aligned, owned by the caller
- * and only read.  T >= 0 (T = 0 is a no-op).  Asynchronous on stream. */
+ * complex voltages of the plan's dtype, owned by the caller and only read,
+ * aligned to its element size (2 bytes for int8, 8 for float32; 16 bytes for
+ * mixed-precision plans).  T >= 0 (T = 0 is a no-op).  Asynchronous on stream. */
 omni_status omni_correlate(omni_plan* plan, const void* volts_dev, int64_t T, void* stream);
 
 /* Same as omni_correlate for voltages in HOST memory (pageable or pinned):

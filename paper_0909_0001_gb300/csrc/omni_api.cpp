@@ -189,6 +189,12 @@ struct omni_plan {
     };
     std::vector<Pending> pending;
     std::vector<cudaEvent_t> event_pool;
+    // batch plan: runs of same-shape arrays, each correlated by one member plan
+    // whose channels are (array, channel) pairs
+    std::vector<omni_plan*> members;
+    std::vector<int> member_arrays;      // arrays per member
+    std::vector<int64_t> array_antennas;  // per array
+    std::vector<int64_t> array_lags;      // per array
 };
 
 namespace {
@@ -388,6 +394,8 @@ void choose_chunks(omni_plan* pl) {
 }
 
 void release(omni_plan* pl) {
+    for (omni_plan* sub : pl->members) release(sub);
+    pl->members.clear();
     DeviceGuard dg(pl->device);
     if (pl->copy_stream) cudaStreamSynchronize(pl->copy_stream);
     cudaFree(pl->buf[0]);
@@ -709,6 +717,72 @@ omni_status omni_plan_create(const omni_level* levels, int n_levels, int64_t n_c
     return OMNI_OK;
 }
 
+omni_status omni_plan_create_batch(const omni_level* const* levels_per_array,
+                                   const int* n_levels_per_array, int n_arrays, int64_t n_channels,
+                                   omni_dtype dtype, omni_precision precision, omni_plan** out) {
+    if (!out) return fail(OMNI_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!levels_per_array || !n_levels_per_array || n_arrays < 1)
+        return fail(OMNI_ERR_INVALID_ARG, "need n_arrays >= 1 and non-NULL level lists");
+    if (n_channels < 1) return fail(OMNI_ERR_INVALID_ARG, "n_channels must be >= 1");
+    std::vector<Geometry> geos(n_arrays);
+    for (int a = 0; a < n_arrays; ++a) {
+        omni_status st = make_geometry(levels_per_array[a], n_levels_per_array[a], geos[a]);
+        if (st == OMNI_OK) st = check_unique(geos[a]);
+        if (st != OMNI_OK) {
+            fail(st, "array %d: %s", a, omni_last_error());
+            return st;
+        }
+    }
+    omni_plan* pl = new omni_plan();
+    pl->C = n_channels;
+    pl->dtype = dtype;
+    pl->precision = precision;
+    cudaGetDevice(&pl->device);
+    for (int a = 0; a < n_arrays; ++a) {
+        pl->array_antennas.push_back(geos[a].N);
+        pl->array_lags.push_back(geos[a].Q);
+    }
+    auto same_shape = [&](int x, int y) {
+        if (geos[x].D != geos[y].D) return false;
+        for (int d = 0; d < geos[x].D; ++d)
+            if (geos[x].n[d] != geos[y].n[d]) return false;
+        return true;
+    };
+    for (int a = 0; a < n_arrays;) {
+        int b = a + 1;
+        while (b < n_arrays && same_shape(a, b)) ++b;
+        omni_plan* sub = nullptr;
+        omni_status st = omni_plan_create(levels_per_array[a], n_levels_per_array[a],
+                                          (int64_t)(b - a) * n_channels, dtype, precision, &sub);
+        if (st != OMNI_OK) {
+            release(pl);
+            return st;
+        }
+        pl->members.push_back(sub);
+        pl->member_arrays.push_back(b - a);
+        a = b;
+    }
+    *out = pl;
+    return OMNI_OK;
+}
+
+omni_status omni_batch_info(const omni_plan* pl, int* n_arrays, int64_t* antennas, int64_t* lags) {
+    if (!pl) return fail(OMNI_ERR_INVALID_ARG, "plan is NULL");
+    if (pl->members.empty()) {
+        if (n_arrays) *n_arrays = 1;
+        if (antennas) antennas[0] = pl->g.N;
+        if (lags) lags[0] = pl->g.Q;
+        return OMNI_OK;
+    }
+    if (n_arrays) *n_arrays = (int)pl->array_antennas.size();
+    for (size_t a = 0; a < pl->array_antennas.size(); ++a) {
+        if (antennas) antennas[a] = pl->array_antennas[a];
+        if (lags) lags[a] = pl->array_lags[a];
+    }
+    return OMNI_OK;
+}
+
 void omni_plan_destroy(omni_plan* plan) {
     if (plan) release(plan);
 }
@@ -716,6 +790,18 @@ void omni_plan_destroy(omni_plan* plan) {
 omni_status omni_plan_info(const omni_plan* pl, int* n_dims, int32_t* dims, int32_t* padded,
                            int64_t* n_antennas, int64_t* n_lags, int64_t* n_channels) {
     if (!pl) return fail(OMNI_ERR_INVALID_ARG, "plan is NULL");
+    if (!pl->members.empty()) {
+        int64_t N = 0, Q = 0;
+        for (size_t a = 0; a < pl->array_antennas.size(); ++a) {
+            N += pl->array_antennas[a];
+            Q += pl->array_lags[a];
+        }
+        if (n_dims) *n_dims = 0;
+        if (n_antennas) *n_antennas = N;
+        if (n_lags) *n_lags = Q;
+        if (n_channels) *n_channels = pl->C;
+        return OMNI_OK;
+    }
     if (n_dims) *n_dims = pl->g.D;
     for (int d = 0; d < pl->g.D; ++d) {
         if (dims) dims[d] = pl->g.n[d];
@@ -730,10 +816,23 @@ omni_status omni_plan_info(const omni_plan* pl, int* n_dims, int32_t* dims, int3
 omni_status omni_correlate(omni_plan* pl, const void* volts_dev, int64_t T, void* stream) {
     omni_status st = check_plan(pl);
     if (st != OMNI_OK) return st;
+    if (!pl->members.empty()) {
+        if (T < 0) return fail(OMNI_ERR_INVALID_ARG, "T must be >= 0");
+        const char* p = (const char*)volts_dev;
+        for (size_t m = 0; m < pl->members.size(); ++m) {
+            omni_plan* sub = pl->members[m];
+            if ((st = omni_correlate(sub, p, T, stream)) != OMNI_OK) return st;
+            p += (size_t)sub->C * T * sub->g.N * elem_bytes(sub->dtype);
+        }
+        return OMNI_OK;
+    }
     if (T < 0) return fail(OMNI_ERR_INVALID_ARG, "T must be >= 0");
     if (T == 0) return OMNI_OK;
     if (!volts_dev) return fail(OMNI_ERR_INVALID_ARG, "volts_dev is NULL");
-    if ((uintptr_t)volts_dev % 16 != 0) return fail(OMNI_ERR_INVALID_ARG, "volts_dev must be 16-byte aligned");
+    if ((uintptr_t)volts_dev % elem_bytes(pl->dtype) != 0)
+        return fail(OMNI_ERR_INVALID_ARG, "volts_dev must be aligned to its element size");
+    if (pl->precision == OMNI_MIXED_FP16 && (uintptr_t)volts_dev % 16 != 0)
+        return fail(OMNI_ERR_INVALID_ARG, "mixed-precision plans need 16-byte aligned volts_dev");
     DeviceGuard dg(pl->device);
     cudaStream_t s = (cudaStream_t)stream;
     for (int64_t c0 = 0; c0 < pl->C; c0 += pl->Cc) {
@@ -750,6 +849,16 @@ omni_status omni_correlate(omni_plan* pl, const void* volts_dev, int64_t T, void
 omni_status omni_correlate_host(omni_plan* pl, const void* volts_host, int64_t T, void* stream) {
     omni_status st = check_plan(pl);
     if (st != OMNI_OK) return st;
+    if (!pl->members.empty()) {
+        if (T < 0) return fail(OMNI_ERR_INVALID_ARG, "T must be >= 0");
+        const char* p = (const char*)volts_host;
+        for (size_t m = 0; m < pl->members.size(); ++m) {
+            omni_plan* sub = pl->members[m];
+            if ((st = omni_correlate_host(sub, p, T, stream)) != OMNI_OK) return st;
+            p += (size_t)sub->C * T * sub->g.N * elem_bytes(sub->dtype);
+        }
+        return OMNI_OK;
+    }
     if (T < 0) return fail(OMNI_ERR_INVALID_ARG, "T must be >= 0");
     if (T == 0) return OMNI_OK;
     if (!volts_host) return fail(OMNI_ERR_INVALID_ARG, "volts_host is NULL");
@@ -806,6 +915,14 @@ omni_status omni_correlate_host(omni_plan* pl, const void* volts_host, int64_t T
 omni_status omni_visibilities(omni_plan* pl, double* vis_dev, int reset, void* stream) {
     omni_status st = check_plan(pl);
     if (st != OMNI_OK) return st;
+    if (!pl->members.empty()) {
+        double* v = vis_dev;
+        for (omni_plan* sub : pl->members) {
+            if ((st = omni_visibilities(sub, v, reset, stream)) != OMNI_OK) return st;
+            v += 2 * sub->C * sub->g.Q;
+        }
+        return OMNI_OK;
+    }
     if (!vis_dev) return fail(OMNI_ERR_INVALID_ARG, "vis_dev is NULL");
     if ((uintptr_t)vis_dev % 16 != 0) return fail(OMNI_ERR_INVALID_ARG, "vis_dev must be 16-byte aligned");
     DeviceGuard dg(pl->device);
@@ -820,6 +937,14 @@ omni_status omni_visibilities(omni_plan* pl, double* vis_dev, int reset, void* s
 omni_status omni_visibilities_host(omni_plan* pl, double* vis_host, int reset, void* stream) {
     omni_status st = check_plan(pl);
     if (st != OMNI_OK) return st;
+    if (!pl->members.empty()) {
+        double* v = vis_host;
+        for (omni_plan* sub : pl->members) {
+            if ((st = omni_visibilities_host(sub, v, reset, stream)) != OMNI_OK) return st;
+            v += 2 * sub->C * sub->g.Q;
+        }
+        return OMNI_OK;
+    }
     if (!vis_host) return fail(OMNI_ERR_INVALID_ARG, "vis_host is NULL");
     DeviceGuard dg(pl->device);
     cudaStream_t s = (cudaStream_t)stream;
@@ -836,6 +961,11 @@ omni_status omni_visibilities_host(omni_plan* pl, double* vis_host, int reset, v
 omni_status omni_reset(omni_plan* pl, void* stream) {
     omni_status st = check_plan(pl);
     if (st != OMNI_OK) return st;
+    if (!pl->members.empty()) {
+        for (omni_plan* sub : pl->members)
+            if ((st = omni_reset(sub, stream)) != OMNI_OK) return st;
+        return OMNI_OK;
+    }
     DeviceGuard dg(pl->device);
     OMNI_CUDA(cudaMemsetAsync(pl->P, 0, (size_t)pl->C * pl->g.L * sizeof(double), (cudaStream_t)stream),
               "cudaMemsetAsync");
@@ -853,6 +983,8 @@ omni_status omni_sync(omni_plan* pl, void* stream) {
 omni_status omni_profile_enable(omni_plan* pl, int enable) {
     omni_status st = check_plan(pl);
     if (st != OMNI_OK) return st;
+    for (omni_plan* sub : pl->members)
+        if ((st = omni_profile_enable(sub, enable)) != OMNI_OK) return st;
     pl->profiling = enable != 0;
     return OMNI_OK;
 }
@@ -860,6 +992,26 @@ omni_status omni_profile_enable(omni_plan* pl, int enable) {
 omni_status omni_profile_read(omni_plan* pl, omni_kernel_stat* out, int max, int* n_out, int clear) {
     omni_status st = check_plan(pl);
     if (st != OMNI_OK) return st;
+    if (!pl->members.empty()) {
+        // members' statistics one after another, names prefixed with the member index
+        int total = 0;
+        for (size_t m = 0; m < pl->members.size(); ++m) {
+            int n = 0;
+            const int room = std::max(0, max - total);
+            if ((st = omni_profile_read(pl->members[m], out ? out + std::min(total, max) : nullptr, room,
+                                        &n, clear)) != OMNI_OK)
+                return st;
+            if (out)
+                for (int i = total; i < std::min(total + n, max); ++i) {
+                    char buf[64];
+                    snprintf(buf, sizeof buf, "a%zu %s", m, out[i].name);
+                    memcpy(out[i].name, buf, sizeof buf);
+                }
+            total += n;
+        }
+        if (n_out) *n_out = total;
+        return OMNI_OK;
+    }
     DeviceGuard dg(pl->device);
     for (auto& q : pl->pending) {
         OMNI_CUDA(cudaEventSynchronize(q.stop), "cudaEventSynchronize");

@@ -32,6 +32,7 @@ EXPORTS = (
     "omni_plan_info", "omni_correlate", "omni_correlate_host", "omni_visibilities",
     "omni_visibilities_host", "omni_reset", "omni_sync", "omni_last_error",
     "omni_status_string", "omni_profile_enable", "omni_profile_read", "omni_correlate_noalloc",
+    "omni_plan_create_batch", "omni_batch_info",
 )
 
 
@@ -82,6 +83,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "omni_last_error": (ctypes.c_char_p, []),
         "omni_status_string": (ctypes.c_char_p, [ctypes.c_int]),
         "omni_profile_enable": (ctypes.c_int, [vp, ctypes.c_int]),
+        "omni_plan_create_batch": (ctypes.c_int, [P(lv), P(ctypes.c_int), ctypes.c_int, i64,
+                                                  ctypes.c_int, ctypes.c_int, P(vp)]),
+        "omni_batch_info": (ctypes.c_int, [vp, P(ctypes.c_int), P(i64), P(i64)]),
         "omni_correlate_noalloc": (ctypes.c_int, [lv, ctypes.c_int, i64, ctypes.c_int, vp, i64,
                                                   vp, vp]),
         "omni_profile_read": (ctypes.c_int, [vp, P(omni_kernel_stat), ctypes.c_int,
@@ -269,3 +273,101 @@ class Plan:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class BatchPlan(Plan):
+    """Several independent arrays (possibly of different hierarchies), C channels each.
+
+    Voltages are passed as one flat tensor holding the arrays' [C][T][N_a][2]
+    blocks one after another (see pack()); visibilities come back as one flat
+    complex128 tensor of the arrays' [C][Q_a] blocks (see unpack())."""
+
+    def __init__(self, arrays: Sequence[Sequence[Level]], channels: int, dtype: str = "cf32",
+                 precision: str = "fp32"):
+        self.arrays = [list(a) for a in arrays]
+        self.channels = int(channels)
+        self.dtype = dtype
+        self.precision = precision
+        n = len(self.arrays)
+        keep = [_levels(a) for a in self.arrays]
+        ptrs = (ctypes.POINTER(omni_level) * n)(*[ctypes.cast(k, ctypes.POINTER(omni_level))
+                                                   for k in keep])
+        nl = (ctypes.c_int * n)(*[len(a) for a in self.arrays])
+        h = ctypes.c_void_p()
+        _check(load().omni_plan_create_batch(ptrs, nl, n, self.channels, DTYPES[dtype],
+                                             PRECISIONS[precision], ctypes.byref(h)))
+        self._h = h
+        na = ctypes.c_int()
+        N = (ctypes.c_int64 * n)()
+        Q = (ctypes.c_int64 * n)()
+        _check(load().omni_batch_info(h, ctypes.byref(na), N, Q))
+        self.antennas = list(N)
+        self.lags = list(Q)
+        self.n_antennas = sum(self.antennas)
+        self.n_lags = sum(self.lags)
+
+    def pack(self, volts: Sequence[torch.Tensor]) -> torch.Tensor:
+        """Concatenate per-array voltages [C][T][N_a][2] into the flat batch layout."""
+        if len(volts) != len(self.arrays):
+            raise ValueError("one voltage tensor per array")
+        T = int(volts[0].shape[1])
+        for v, N in zip(volts, self.antennas):
+            if tuple(v.shape) != (self.channels, T, N, 2):
+                raise ValueError(f"expected [{self.channels}][{T}][{N}][2], got {tuple(v.shape)}")
+        return torch.cat([v.reshape(-1) for v in volts])
+
+    def samples_of(self, flat: torch.Tensor) -> int:
+        per = self.channels * self.n_antennas * 2
+        if flat.dim() != 1 or flat.numel() % per:
+            raise ValueError("flat batch voltages must be 1-D with C * T * sum(N_a) * 2 values")
+        return flat.numel() // per
+
+    def unpack(self, vis: torch.Tensor) -> list:
+        """Split flat visibilities into per-array [C][Q_a] views."""
+        out, off = [], 0
+        for Q in self.lags:
+            out.append(vis[off:off + self.channels * Q].view(self.channels, Q))
+            off += self.channels * Q
+        return out
+
+    def _flat(self, volts: torch.Tensor) -> int:
+        want = torch.int8 if self.dtype == "ci8" else torch.float32
+        if volts.dtype != want or not volts.is_contiguous():
+            raise TypeError(f"flat batch voltages must be contiguous {want}")
+        return self.samples_of(volts)
+
+    def correlate(self, volts: torch.Tensor, stream=None) -> None:
+        if not volts.is_cuda:
+            raise ValueError("correlate() takes device voltages; use correlate_host()")
+        T = self._flat(volts)
+        _check(load().omni_correlate(self._h, ctypes.c_void_p(volts.data_ptr()), T,
+                                     _stream_ptr(stream)))
+
+    def correlate_host(self, volts: torch.Tensor, stream=None) -> None:
+        if volts.is_cuda:
+            raise ValueError("correlate_host() takes host voltages")
+        T = self._flat(volts)
+        _check(load().omni_correlate_host(self._h, ctypes.c_void_p(volts.data_ptr()), T,
+                                          _stream_ptr(stream)))
+
+    def visibilities(self, reset: bool = True, out: Optional[torch.Tensor] = None,
+                     stream=None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty(self.channels * self.n_lags, dtype=torch.complex128, device="cuda")
+        if out.dtype != torch.complex128 or not out.is_cuda or not out.is_contiguous() \
+                or out.numel() != self.channels * self.n_lags:
+            raise ValueError("out must be a contiguous complex128 CUDA tensor of C*sum(Q_a)")
+        _check(load().omni_visibilities(self._h, ctypes.c_void_p(out.data_ptr()), int(reset),
+                                        _stream_ptr(stream)))
+        return out
+
+    def visibilities_host(self, reset: bool = True, out: Optional[torch.Tensor] = None,
+                          stream=None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty(self.channels * self.n_lags, dtype=torch.complex128)
+        if out.dtype != torch.complex128 or out.is_cuda or not out.is_contiguous() \
+                or out.numel() != self.channels * self.n_lags:
+            raise ValueError("out must be a contiguous complex128 host tensor of C*sum(Q_a)")
+        _check(load().omni_visibilities_host(self._h, ctypes.c_void_p(out.data_ptr()),
+                                             int(reset), _stream_ptr(stream)))
+        return out

@@ -159,6 +159,38 @@ def workload(name: str) -> Workload:
 WORKLOADS = ("grid16", "hier2", "hier3", "grid1024")
 
 
+def batch_arrays(n_arrays: int = 48, seed: int = 9090004) -> List[List[Level]]:
+    """Uneven independent arrays: half single-level squares with side 8..64, half
+    2-level hierarchies of 4x4 tiles on an 8x8 or 16x16 grid, each with a seeded
+    rotation and shear; sorted by shape so that equal shapes are adjacent."""
+    rng = np.random.default_rng(seed)
+    arrays = []
+    for a in range(n_arrays):
+        th = rng.uniform(0.0, math.pi, 2)
+        sh = rng.uniform(-0.3, 0.3, 2)
+        if a < n_arrays // 2:
+            side = int(rng.choice([8, 16, 32, 64]))
+            arrays.append([Level(side, side, sheared_rotation(1.0, th[0], sh[0]))])
+        else:
+            side = int(rng.choice([8, 16]))
+            arrays.append(hierarchy([(4, 4), (side, side)], list(th), list(sh)))
+    arrays.sort(key=lambda lv: (len(lv), [(x.n1, x.n2) for x in lv]))
+    return arrays
+
+
+def batch_voltages(arrays: Sequence[Sequence[Level]], channels: int, samples: int,
+                   dtype: str = "ci8", device: str | torch.device = "cpu",
+                   seed: int = 9090004, n_sources: int = 3) -> List[torch.Tensor]:
+    """Per-array voltages [C][T][N_a][2] with noise sigma 20 and point sources."""
+    out = []
+    for a, levels in enumerate(arrays):
+        w = Workload(f"array{a}", list(levels), channels, samples, dtype, n_sources,
+                     noise_sigma=20.0, source_sigma=10.0, seed=seed + 101 * a,
+                     freq_lo_hz=100e6, freq_hi_hz=200e6)
+        out.append(voltages(w, device=device))
+    return out
+
+
 def paper_fixture(name: str) -> List[Level]:
     """Array layouts printed in the paper."""
     if name == "warmup_1d":        # Sec. II.C: x = 1,2,3,7,8,9 as one 9-long row
