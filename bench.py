@@ -387,10 +387,93 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_batch(args):
+    """Uneven independent arrays in one batch plan vs one plan per array (FP32 path)."""
+    import torch
+    import torch.distributed as dist
+    from paper_0909_0001_gb300 import multirank, omni, synth
+
+    rank, local_rank, world = multirank.rank_env()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    arrays = synth.batch_arrays()
+    C = args.channels or 128
+    T = args.samples or 512
+    volts = synth.batch_voltages(arrays, C, T, device="cuda", seed=9090004 + 1000 * rank)
+    plan = omni.BatchPlan(arrays, C, dtype="ci8")
+    flat = plan.pack(volts)
+    del volts
+    units = plan.n_antennas * C * T
+    stream = torch.cuda.current_stream()
+    vis = torch.empty(C * plan.n_lags, dtype=torch.complex128, device="cuda")
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        ms, stats = timed_steps(plan, flat, vis, args.steps, args.warmup, stream, barrier, True)
+    rate, slowest = multirank.job_rate(units, ms * 1e-3, device=dev)
+    # the same arrays as separate plans, launched one after another
+    sep = None
+    if not args.no_compare:
+        singles, offs, off = [], [], 0
+        for levels, N in zip(arrays, plan.antennas):
+            singles.append(omni.Plan(levels, C, dtype="ci8"))
+            offs.append(off)
+            off += C * T * N * 2
+        views = [flat[o:o + C * T * N * 2].view(C, T, N, 2) for o, N in zip(offs, plan.antennas)]
+        outs = [torch.empty((C, q), dtype=torch.complex128, device="cuda") for q in plan.lags]
+
+        def step_all():
+            for sp, v, o in zip(singles, views, outs):
+                sp.correlate(v)
+                sp.visibilities(reset=True, out=o)
+
+        for _ in range(max(3, args.warmup)):
+            step_all()
+        barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step_all()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sep_ms = e0.elapsed_time(e1) / args.steps
+        sep_rate, sep_s = multirank.job_rate(units, sep_ms * 1e-3, device=dev)
+        sep = {"value": sep_rate, "ms_per_step": sep_s * 1e3, "plans": len(singles)}
+        for sp in singles:
+            sp.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": slowest * 1e3,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": f"{len(arrays)} uneven arrays (single-level 8x8..64x64, "
+                                       "2-level 4x4 tiles on 8x8/16x16 grids), batch plan",
+                           "arrays": len(arrays), "antennas_total": plan.n_antennas,
+                           "channels": C, "samples": T, "input": "ci8", "precision": "fp32",
+                           "shape_groups": len(set(tuple((l.n1, l.n2) for l in a) for a in arrays)),
+                           "l2": "inputs larger than L2 (%.1f GB per step); no flush"
+                                 % (flat.numel() / 1e9)},
+                "roofline": roofline(stats, "batch48", "fp32"),
+                "gpu_launches": sum(s["launches"] for s in stats),
+                "clocks": clk.summary(), "separate_plans": sep}
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch48":
+        run_batch(args)
     else:
         run_ours(args)
 

@@ -172,6 +172,8 @@ struct omni_plan {
     float2* buf[2] = {nullptr, nullptr};
     int64_t buf_elems = 0;
     double* P = nullptr;      // [C][L]
+    int* dev_err = nullptr;   // device error word of bounded waits
+    int force_expire = 0;     // OMNI_TEST_FORCE_TIMEOUT: tensor-core waits expire (tests)
     std::vector<float2*> tw_tables;
     // host-input staging
     void* stage[2] = {nullptr, nullptr};
@@ -282,7 +284,11 @@ omni_status build_passes(omni_plan* pl) {
         pa.outer = (int64_t)g.n[2] * g.n[3];
         Pass pb{};
         pb.axis = 2;
+        // warp-level mma.sync by default (measured faster for these 16-point
+        // DFTs); OMNI_TCGEN05=1 selects the tensor-memory (tcgen05) variant
         pb.kind = KIND_TC_B;
+        if (const char* env = std::getenv("OMNI_TCGEN05"))
+            if (std::atoi(env) != 0) pb.kind = KIND_TC5_B;
         pb.mode = MODE_LAST;
         pb.L = g.Lp[2];
         pb.n = g.n[2];
@@ -370,6 +376,7 @@ void choose_chunks(omni_plan* pl) {
     switch (last.kind) {
         case KIND_LEVEL:
         case KIND_TC_B:
+        case KIND_TC5_B:
         case KIND_SMEM: ctas = (last.inner + last.W - 1) / last.W; break;
         case KIND_REG: ctas = (last.inner + 255) / 256; break;
         default: ctas = (last.L * last.inner + 255) / 256; break;
@@ -380,6 +387,7 @@ void choose_chunks(omni_plan* pl) {
     const int first_src = pl->fwd.size() == 1 ? (pl->dtype == OMNI_IN_CI8 ? SRC_CI8 : SRC_CF32) : SRC_BUF;
     if (last.kind == KIND_LEVEL && level_last_occupancy(last, first_src, &per_sm) != cudaSuccess) per_sm = 0;
     if (last.kind == KIND_TC_B && tc_occupancy(KIND_TC_B, &per_sm) != cudaSuccess) per_sm = 0;
+    if (last.kind == KIND_TC5_B && tc5_occupancy(&per_sm) != cudaSuccess) per_sm = 0;
     cudaGetLastError();
     int64_t slots = (int64_t)std::max(sms, 1) * std::max(per_sm, 2);
     if (sms <= 0) slots = 304;
@@ -393,6 +401,19 @@ void choose_chunks(omni_plan* pl) {
     pl->buf_elems = std::max(pl->Cc * pl->Tc * pl->fwd_elems, pl->Cv * pl->inv_elems);
 }
 
+// After a stream synchronisation: report (and clear) an expired device wait.
+omni_status check_device_error(omni_plan* pl) {
+    if (!pl->dev_err) return OMNI_OK;
+    int h = 0;
+    OMNI_CUDA(cudaMemcpy(&h, pl->dev_err, sizeof(int), cudaMemcpyDeviceToHost), "reading the device error word");
+    if (h) {
+        cudaMemset(pl->dev_err, 0, sizeof(int));
+        return fail(OMNI_ERR_TIMEOUT, "a bounded wait for a tensor-core operation expired; the "
+                                      "accumulated visibilities are incomplete");
+    }
+    return OMNI_OK;
+}
+
 void release(omni_plan* pl) {
     for (omni_plan* sub : pl->members) release(sub);
     pl->members.clear();
@@ -401,6 +422,7 @@ void release(omni_plan* pl) {
     cudaFree(pl->buf[0]);
     cudaFree(pl->buf[1]);
     cudaFree(pl->P);
+    cudaFree(pl->dev_err);
     cudaFree(pl->vis_tmp);
     for (float2* t : pl->tw_tables) cudaFree(t);
     for (int b = 0; b < 2; ++b) {
@@ -419,7 +441,7 @@ void release(omni_plan* pl) {
 
 const char* kind_name(int k) {
     return k == KIND_REG ? "reg" : k == KIND_SMEM ? "smem" : k == KIND_LEVEL ? "level"
-         : k == KIND_TC_A || k == KIND_TC_B ? "tc" : "direct";
+         : k == KIND_TC_A || k == KIND_TC_B ? "tc" : k == KIND_TC5_B ? "tcgen05-" : "direct";
 }
 const char* mode_name(int m) {
     return m == MODE_MID ? "mid" : m == MODE_LAST ? "last" : m == MODE_INV_MID ? "mid" : "last";
@@ -430,13 +452,13 @@ void init_stats(omni_plan* pl) {
     for (int inv = 0; inv < 2; ++inv)
         for (const Pass& p : inv ? pl->inv : pl->fwd) {
             omni_kernel_stat st{};
-            if (p.kind == KIND_LEVEL || p.kind == KIND_TC_A || p.kind == KIND_TC_B)
+            if (p.kind == KIND_LEVEL || p.kind == KIND_TC_A || p.kind == KIND_TC_B || p.kind == KIND_TC5_B)
                 snprintf(st.name, sizeof st.name, "%s axis%d+%d %s%d %s", inv ? "inv" : "fwd", p.axis,
                          p.axis + 1, kind_name(p.kind), p.L, mode_name(p.mode));
             else
                 snprintf(st.name, sizeof st.name, "%s axis%d %s%d %s", inv ? "inv" : "fwd", p.axis,
                          kind_name(p.kind), p.L, mode_name(p.mode));
-            st.tensor = (p.kind == KIND_TC_A || p.kind == KIND_TC_B) ? 1 : 0;
+            st.tensor = (p.kind == KIND_TC_A || p.kind == KIND_TC_B || p.kind == KIND_TC5_B) ? 1 : 0;
             pl->stats.push_back(st);
         }
 }
@@ -460,7 +482,8 @@ double src_bytes(int src_kind) {
 // Algorithmic bytes of one launch: inputs read plus outputs written.
 double pass_bytes(const Pass& p, const PassArgs& a) {
     const double in = src_bytes(a.src_kind);
-    const bool two_axes = p.kind == KIND_LEVEL || p.kind == KIND_TC_A || p.kind == KIND_TC_B;
+    const bool two_axes = p.kind == KIND_LEVEL || p.kind == KIND_TC_A || p.kind == KIND_TC_B ||
+                          p.kind == KIND_TC5_B;
     const double n_in = two_axes ? (double)p.n * p.n : (double)p.n;
     switch (p.mode) {
         case MODE_MID:
@@ -482,6 +505,7 @@ double pass_flops(const Pass& p, const PassArgs& a) {
         case KIND_TC_A:  // per 16x16 block: 32 + 96 products
             return (double)a.S * p.outer * 128.0 * 4096.0;
         case KIND_TC_B:  // per level-1 frequency and sample: 6 + 12 products, |F|^2
+        case KIND_TC5_B:  // the same products as 128x32x16 tiles (18 x 4096 per frequency)
             return (double)a.S * a.tc * p.inner * (18.0 * 4096.0 + 3.0 * p.q_out);
         case KIND_LEVEL: {
             const double per_unit = (double)p.n * line + (double)p.L * line;  // axis a, axis b
@@ -536,6 +560,8 @@ omni_status run_chunk(omni_plan* pl, const void* volts, int64_t vc0, int64_t Tsr
         a.c0 = c0;
         a.P = pl->P;
         a.P_stride = pl->g.L;
+        a.err = pl->dev_err;
+        a.force_expire = pl->force_expire;
         float2* dst = pl->buf[k & 1];
         if (p.mode == MODE_LAST) {
             a.S = cc;
@@ -668,6 +694,7 @@ omni_status omni_plan_create(const omni_level* levels, int n_levels, int64_t n_c
     pl->C = n_channels;
     pl->dtype = dtype;
     pl->precision = precision;
+    if (const char* env = std::getenv("OMNI_TEST_FORCE_TIMEOUT")) pl->force_expire = std::atoi(env) != 0;
     cudaError_t e = cudaGetDevice(&pl->device);
     if (e != cudaSuccess) {
         delete pl;
@@ -709,7 +736,9 @@ omni_status omni_plan_create(const omni_level* levels, int n_levels, int64_t n_c
     if ((e = cudaMalloc(&pl->buf[0], buf_bytes)) != cudaSuccess ||
         (e = cudaMalloc(&pl->buf[1], buf_bytes)) != cudaSuccess ||
         (e = cudaMalloc(&pl->P, P_bytes)) != cudaSuccess ||
-        (e = cudaMemset(pl->P, 0, P_bytes)) != cudaSuccess) {
+        (e = cudaMemset(pl->P, 0, P_bytes)) != cudaSuccess ||
+        (e = cudaMalloc(&pl->dev_err, sizeof(int))) != cudaSuccess ||
+        (e = cudaMemset(pl->dev_err, 0, sizeof(int))) != cudaSuccess) {
         release(pl);
         return cuda_fail(e, "allocating plan buffers");
     }
@@ -931,7 +960,7 @@ omni_status omni_visibilities(omni_plan* pl, double* vis_dev, int reset, void* s
     if (st != OMNI_OK) return st;
     if (reset) OMNI_CUDA(cudaMemsetAsync(pl->P, 0, (size_t)pl->C * pl->g.L * sizeof(double), s), "cudaMemsetAsync");
     OMNI_CUDA(cudaStreamSynchronize(s), "device error during correlation");
-    return OMNI_OK;
+    return check_device_error(pl);
 }
 
 omni_status omni_visibilities_host(omni_plan* pl, double* vis_host, int reset, void* stream) {
@@ -955,7 +984,7 @@ omni_status omni_visibilities_host(omni_plan* pl, double* vis_host, int reset, v
     if (reset) OMNI_CUDA(cudaMemsetAsync(pl->P, 0, (size_t)pl->C * pl->g.L * sizeof(double), s), "cudaMemsetAsync");
     OMNI_CUDA(cudaMemcpyAsync(vis_host, pl->vis_tmp, bytes, cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync(D2H)");
     OMNI_CUDA(cudaStreamSynchronize(s), "device error during correlation");
-    return OMNI_OK;
+    return check_device_error(pl);
 }
 
 omni_status omni_reset(omni_plan* pl, void* stream) {
@@ -977,7 +1006,9 @@ omni_status omni_sync(omni_plan* pl, void* stream) {
     if (st != OMNI_OK) return st;
     DeviceGuard dg(pl->device);
     OMNI_CUDA(cudaStreamSynchronize((cudaStream_t)stream), "device error");
-    return OMNI_OK;
+    for (omni_plan* sub : pl->members)
+        if ((st = check_device_error(sub)) != OMNI_OK) return st;
+    return check_device_error(pl);
 }
 
 omni_status omni_profile_enable(omni_plan* pl, int enable) {

@@ -36,6 +36,7 @@ cudaError_t launch_pass(const Pass& p, const PassArgs& a, cudaStream_t st) {
         case KIND_LEVEL: return p.L <= 16 ? launch_level_a(p, a, st) : launch_level_b(p, a, st);
         case KIND_TC_A:
         case KIND_TC_B: return launch_tc(p, a, st);
+        case KIND_TC5_B: return launch_tc5(p, a, st);
         default: return launch_direct(p, a, st);
     }
 }
@@ -64,6 +65,7 @@ cudaError_t init_device_tables() {
                     upload_twiddles_level_b})
         if ((e = up()) != cudaSuccess) return e;
     if ((e = upload_tc_tables()) != cudaSuccess) return e;
+    if ((e = upload_tc5_tables()) != cudaSuccess) return e;
     done.push_back(dev);
     return cudaSuccess;
 }

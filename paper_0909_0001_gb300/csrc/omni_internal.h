@@ -32,7 +32,8 @@ enum PassKind : int {
     KIND_DIRECT = 2, // direct DFT from a twiddle table (any length)
     KIND_LEVEL = 3,  // both axes of one square level (L_a = L_b <= 64) in shared memory
     KIND_TC_A = 4,   // mixed precision, finest level as split-FP16 tensor-core GEMMs
-    KIND_TC_B = 5    // mixed precision, coarse level + |F|^2 as tensor-core GEMMs (LAST)
+    KIND_TC_B = 5,   // mixed precision, coarse level + |F|^2 as tensor-core GEMMs (LAST, mma.sync)
+    KIND_TC5_B = 6   // the same on 5th-generation tensor cores (tcgen05, tensor memory)
 };
 
 // One axis transform.  The data of one sample (or channel) is viewed as
@@ -72,6 +73,8 @@ struct PassArgs {
     double2* V;          // INV_LAST output
     int64_t V_stride;    // lags per channel
     double scale;        // INV_LAST: 1/L
+    int* err;            // device error word (bounded waits that expired set it to 1)
+    int force_expire;    // test hook: make the first bounded wait expire
 };
 
 // Upload the twiddle tables to the current device (once per device).
@@ -91,6 +94,9 @@ bool tc_supports(const int32_t* n, int D, int dtype_is_ci8);
 cudaError_t upload_tc_tables();
 cudaError_t tc_occupancy(int kind, int* blocks_per_sm);
 cudaError_t launch_tc(const Pass& p, const PassArgs& a, cudaStream_t stream);
+cudaError_t upload_tc5_tables();
+cudaError_t tc5_occupancy(int* blocks_per_sm);
+cudaError_t launch_tc5(const Pass& p, const PassArgs& a, cudaStream_t stream);
 
 // Set the calling thread's omni_last_error() message.
 void set_last_error(const char* msg);

@@ -303,3 +303,32 @@ def test_mixed_rejects_unsupported_shapes():
     assert e.value.status == 3
     with pytest.raises(omni.OmniError):
         omni.Plan([synth.Level(16, 16)], 1, dtype="ci8", precision="mixed")
+
+
+def test_mixed_tcgen05_variant(monkeypatch):
+    """The tensor-memory (tcgen05) stage B gives the same visibilities."""
+    w = synth.workload("hier2")
+    x = synth.voltages(w, channels=2, samples=9)
+    default = gpu_vis(w.levels, x, dtype="ci8", precision="mixed")
+    monkeypatch.setenv("OMNI_TCGEN05", "1")
+    V, _ = check(w.levels, x, dtype="ci8", tol=TOL_MIXED, precision="mixed")
+    assert relerr_per_channel(V, default) <= 1e-6
+
+
+def test_expired_tensor_core_wait_is_reported(monkeypatch):
+    """A bounded device wait that runs out returns OMNI_ERR_TIMEOUT; the context stays usable.
+
+    The test hook makes the first tcgen05 wait wait for a phase that never comes,
+    with a budget of ~0.5 ms, so nothing hangs or faults."""
+    w = synth.workload("hier2")
+    x = synth.voltages(w, channels=1, samples=3).cuda()
+    monkeypatch.setenv("OMNI_TCGEN05", "1")
+    monkeypatch.setenv("OMNI_TEST_FORCE_TIMEOUT", "1")
+    with omni.Plan(w.levels, 1, dtype="ci8", precision="mixed") as plan:
+        plan.correlate(x)
+        with pytest.raises(omni.OmniError) as e:
+            plan.visibilities()
+        assert e.value.status == 6
+    monkeypatch.delenv("OMNI_TEST_FORCE_TIMEOUT")
+    V = gpu_vis(w.levels, x.cpu(), dtype="ci8", precision="mixed")
+    assert np.isfinite(V).all()
