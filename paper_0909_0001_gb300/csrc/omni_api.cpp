@@ -181,6 +181,13 @@ struct omni_plan {
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t ready[2] = {nullptr, nullptr};
     cudaEvent_t freed[2] = {nullptr, nullptr};
+    // two-pass plans: the first pass of chunk j+1 runs on aux_stream while the
+    // last pass of chunk j runs on the caller's stream (double-buffered scratch)
+    bool overlap = false;
+    cudaStream_t aux_stream = nullptr;
+    cudaEvent_t mid_done[2] = {nullptr, nullptr};
+    cudaEvent_t last_done[2] = {nullptr, nullptr};
+    cudaEvent_t start_ev = nullptr;
     double2* vis_tmp = nullptr;  // device staging for omni_visibilities_host
     // statistics per pass: forward passes first, then inverse passes
     std::vector<omni_kernel_stat> stats;
@@ -431,6 +438,15 @@ void release(omni_plan* pl) {
         if (pl->freed[b]) cudaEventDestroy(pl->freed[b]);
     }
     if (pl->copy_stream) cudaStreamDestroy(pl->copy_stream);
+    if (pl->aux_stream) {
+        cudaStreamSynchronize(pl->aux_stream);
+        cudaStreamDestroy(pl->aux_stream);
+    }
+    if (pl->start_ev) cudaEventDestroy(pl->start_ev);
+    for (int b = 0; b < 2; ++b) {
+        if (pl->mid_done[b]) cudaEventDestroy(pl->mid_done[b]);
+        if (pl->last_done[b]) cudaEventDestroy(pl->last_done[b]);
+    }
     for (auto& q : pl->pending) {
         cudaEventDestroy(q.start);
         cudaEventDestroy(q.stop);
@@ -542,7 +558,7 @@ cudaError_t launch_counted(omni_plan* pl, int idx, const Pass& p, const PassArgs
 
 // One chunk of forward passes: channels [c0, c0+cc) x samples [t0, t0+tc).
 omni_status run_chunk(omni_plan* pl, const void* volts, int64_t vc0, int64_t Tsrc, int64_t t0,
-                      int64_t c0, int64_t cc, int64_t tc, cudaStream_t st) {
+                      int64_t c0, int64_t cc, int64_t tc, cudaStream_t st, int slot = -1) {
     const void* src = volts;
     int src_kind = pl->dtype == OMNI_IN_CI8 ? SRC_CI8 : SRC_CF32;
     int64_t src_stride = 0;
@@ -562,7 +578,14 @@ omni_status run_chunk(omni_plan* pl, const void* volts, int64_t vc0, int64_t Tsr
         a.P_stride = pl->g.L;
         a.err = pl->dev_err;
         a.force_expire = pl->force_expire;
-        float2* dst = pl->buf[k & 1];
+        float2* dst = pl->buf[slot >= 0 ? slot : (int)(k & 1)];
+        cudaStream_t launch_stream = st;
+        if (slot >= 0 && p.mode == MODE_MID) {
+            // first pass of an overlapped chunk: on the aux stream, after the last
+            // pass that read this buffer two chunks ago
+            launch_stream = pl->aux_stream;
+            OMNI_CUDA(cudaStreamWaitEvent(launch_stream, pl->last_done[slot], 0), "cudaStreamWaitEvent");
+        }
         if (p.mode == MODE_LAST) {
             a.S = cc;
         } else {
@@ -570,8 +593,13 @@ omni_status run_chunk(omni_plan* pl, const void* volts, int64_t vc0, int64_t Tsr
             a.dst = dst;
             a.dst_stride = p.outer * p.q_out * p.inner;
         }
-        cudaError_t e = launch_counted(pl, (int)k, p, a, st);
+        if (slot >= 0 && p.mode == MODE_LAST)
+            OMNI_CUDA(cudaStreamWaitEvent(st, pl->mid_done[slot], 0), "cudaStreamWaitEvent");
+        cudaError_t e = launch_counted(pl, (int)k, p, a, launch_stream);
         if (e != cudaSuccess) return cuda_fail(e, "forward pass launch");
+        if (slot >= 0)
+            OMNI_CUDA(cudaEventRecord(p.mode == MODE_MID ? pl->mid_done[slot] : pl->last_done[slot],
+                                      launch_stream), "cudaEventRecord");
         src = dst;
         src_kind = SRC_BUF;
         src_stride = p.outer * p.q_out * p.inner;
@@ -711,6 +739,22 @@ omni_status omni_plan_create(const omni_level* levels, int n_levels, int64_t n_c
         return st;
     }
     choose_chunks(pl);
+    // overlap the two passes of consecutive chunks (OMNI_OVERLAP=0 turns it off)
+    pl->overlap = pl->fwd.size() == 2;
+    if (const char* env = std::getenv("OMNI_OVERLAP")) pl->overlap = pl->overlap && std::atoi(env) != 0;
+    if (pl->overlap) {
+        if ((e = cudaStreamCreateWithFlags(&pl->aux_stream, cudaStreamNonBlocking)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&pl->start_ev, cudaEventDisableTiming)) != cudaSuccess) {
+            release(pl);
+            return cuda_fail(e, "creating the overlap stream");
+        }
+        for (int b = 0; b < 2; ++b)
+            if ((e = cudaEventCreateWithFlags(&pl->mid_done[b], cudaEventDisableTiming)) != cudaSuccess ||
+                (e = cudaEventCreateWithFlags(&pl->last_done[b], cudaEventDisableTiming)) != cudaSuccess) {
+                release(pl);
+                return cuda_fail(e, "creating the overlap events");
+            }
+    }
     // persistent finest-level passes: one wave of resident CTAs
     for (size_t k = 0; k < pl->fwd.size(); ++k) {
         Pass& p = pl->fwd[k];
@@ -864,11 +908,18 @@ omni_status omni_correlate(omni_plan* pl, const void* volts_dev, int64_t T, void
         return fail(OMNI_ERR_INVALID_ARG, "mixed-precision plans need 16-byte aligned volts_dev");
     DeviceGuard dg(pl->device);
     cudaStream_t s = (cudaStream_t)stream;
+    if (pl->overlap) {
+        // the aux stream starts after everything already queued on the caller's stream
+        OMNI_CUDA(cudaEventRecord(pl->start_ev, s), "cudaEventRecord");
+        OMNI_CUDA(cudaStreamWaitEvent(pl->aux_stream, pl->start_ev, 0), "cudaStreamWaitEvent");
+        for (int b = 0; b < 2; ++b) OMNI_CUDA(cudaEventRecord(pl->last_done[b], s), "cudaEventRecord");
+    }
+    int64_t j = 0;
     for (int64_t c0 = 0; c0 < pl->C; c0 += pl->Cc) {
         const int64_t cc = std::min(pl->Cc, pl->C - c0);
-        for (int64_t t0 = 0; t0 < T; t0 += pl->Tc) {
+        for (int64_t t0 = 0; t0 < T; t0 += pl->Tc, ++j) {
             const int64_t tc = std::min(pl->Tc, T - t0);
-            st = run_chunk(pl, volts_dev, c0, T, t0, c0, cc, tc, s);
+            st = run_chunk(pl, volts_dev, c0, T, t0, c0, cc, tc, s, pl->overlap ? (int)(j & 1) : -1);
             if (st != OMNI_OK) return st;
         }
     }
