@@ -21,6 +21,8 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+
+import numpy as np
 import json
 import os
 import statistics
@@ -333,6 +335,27 @@ def run_ours(args):
     head = results[args.precision]
     plan, vis = head["plan"], head["vis"]
 
+    # physical-baseline epilogue: radial profile of the step's visibilities
+    epilogue = None
+    if rank == 0:
+        n_bins = 256
+        rmax = max(float(np.hypot(*omni.baselines(w.levels)[2].T).max()), 1.0)
+        bins, _ = omni.radial_bins(w.levels, rmax / n_bins * 1.0001, n_bins)
+        gbins = torch.from_numpy(bins).cuda()
+        prof = torch.empty((w.channels, n_bins), dtype=torch.complex128, device="cuda")
+        omni.sum_groups(vis, gbins, n_bins, out=prof)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 10
+        e0.record(stream)
+        for _ in range(reps):
+            omni.sum_groups(vis, gbins, n_bins, out=prof)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_e = e0.elapsed_time(e1) / reps
+        nbytes = vis.numel() * 16 + bins.size * 4 + prof.numel() * 16
+        epilogue = {"radial_profile_ms": ms_e, "bins": n_bins, "lags": int(vis.shape[1]),
+                    "GB_per_s": nbytes / (ms_e * 1e-3) / 1e9}
+
     # end to end through the host-buffer entry points
     e2e = None
     if not args.no_e2e:
@@ -374,7 +397,7 @@ def run_ours(args):
                 "roofline": roofline(stats, args.workload, args.precision),
                 "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": sum(s["launches"] for s in stats),
-                "clocks": clocks,
+                "clocks": clocks, "epilogue": epilogue,
                 "kernels": [{k: s[k] for k in ("name", "launches", "total_ms")}
                             for s in stats if s["launches"]]}
         if "fp32" in results and args.precision != "fp32":

@@ -187,6 +187,37 @@ omni_status omni_profile_enable(omni_plan* plan, int enable);
 omni_status omni_profile_read(omni_plan* plan, omni_kernel_stat* out, int max, int* n_out,
                               int clear);
 
+/* ---- Physical-baseline epilogue (Sec. II.D, Sec. III) ----
+ * The hypercube output has one value per 2n-D lag; lags whose physical
+ * baselines dr = sum_k A_k (D_{2k}, D_{2k+1}) coincide (possible for
+ * interleaved hierarchies, Sec. II.D) measure the same uv point, and binning
+ * |dr| radially gives the one-dimensional baseline distribution (Figs. 2-5,
+ * bottom panels, for a layout map of ones). */
+
+/* Radial bins (host only, no GPU): bin_of_lag[q] = floor(|dr_q| / bin_width)
+ * for lags inside the first n_bins bins, else -1; pairs_per_bin[b] = number of
+ * antenna pairs in bin b (sum of the lags' redundancies).  Either output may
+ * be NULL. */
+omni_status omni_radial_bins(const omni_level* levels, int n_levels, double bin_width,
+                             int64_t n_bins, int32_t* bin_of_lag, int64_t* pairs_per_bin);
+
+/* Distinct physical baselines (host only, no GPU): lags whose dr agree within
+ * 1e-9 * max|dr| share a group; groups are numbered in order of their first
+ * lag.  n_unique receives the group count; group_of_lag [n_lags];
+ * dr_unique [n_lags][2] and pairs_unique [n_lags] (first n_unique entries
+ * used) receive each group's baseline and antenna-pair count.  Outputs other
+ * than n_unique may be NULL. */
+omni_status omni_unique_baselines(const omni_level* levels, int n_levels, int64_t* n_unique,
+                                  int32_t* group_of_lag, double* dr_unique, int64_t* pairs_unique);
+
+/* Sum visibilities by group on the GPU: out[c][g] = sum of vis[c][q] over
+ * the lags q with group_dev[q] == g (group -1: skipped).  vis_dev: DEVICE
+ * [C][Q] complex128; group_dev: DEVICE [Q] int32; out_dev: DEVICE
+ * [C][n_groups] complex128, overwritten.  FP64 sums (atomic, so the order of
+ * the additions is not fixed).  Asynchronous on stream. */
+omni_status omni_sum_groups(const double* vis_dev, int64_t C, int64_t Q, const int32_t* group_dev,
+                            int64_t n_groups, double* out_dev, void* stream);
+
 /* Size of the device array that omni_correlate_noalloc uses as scratch. */
 #define OMNI_NOALLOC_SCRATCH_BYTES (64ull * 1024ull * 1024ull)
 

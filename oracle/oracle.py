@@ -165,3 +165,49 @@ def correlate_selected(dims: Sequence[int], x, chans, lag_idx) -> np.ndarray:
                                     _ptr(ch, ctypes.c_int64), _ptr(lq, ctypes.c_int64),
                                     _ptr(V, ctypes.c_double))
     return V[:, 0] + 1j * V[:, 1]
+
+
+# ---------------------------------------------------------------- physical baselines
+
+def radial_bins(levels, bin_width: float, n_bins: int):
+    """Radial bin of every lag, floor(|dr| / bin_width) (or -1 beyond n_bins), and
+    the antenna pairs per bin: the radially binned baseline distribution of Sec. III."""
+    dims = [v for lv in levels for v in (lv.n1, lv.n2)]
+    dm, red = lag_table(dims)
+    dr = baseline_vectors(levels, dm)
+    b = np.floor(np.hypot(dr[:, 0], dr[:, 1]) / bin_width)
+    b = np.where(b < n_bins, b, -1).astype(np.int64)
+    pairs = np.zeros(n_bins, dtype=np.int64)
+    for q in range(len(b)):
+        if b[q] >= 0:
+            pairs[b[q]] += red[q]
+    return b.astype(np.int32), pairs
+
+
+def unique_baselines(levels, tol_rel: float = 1e-9):
+    """Lags grouped by coincident physical baseline (plain loop over existing groups)."""
+    dims = [v for lv in levels for v in (lv.n1, lv.n2)]
+    dm, red = lag_table(dims)
+    dr = baseline_vectors(levels, dm)
+    tol = tol_rel * float(np.max(np.hypot(dr[:, 0], dr[:, 1])))
+    reps, pairs, group = [], [], np.zeros(len(dr), dtype=np.int32)
+    for q in range(len(dr)):
+        for g, r in enumerate(reps):
+            if np.hypot(dr[q, 0] - r[0], dr[q, 1] - r[1]) <= tol:
+                group[q] = g
+                pairs[g] += red[q]
+                break
+        else:
+            group[q] = len(reps)
+            reps.append(dr[q])
+            pairs.append(int(red[q]))
+    return group, np.array(reps), np.array(pairs, dtype=np.int64)
+
+
+def group_sum(V: np.ndarray, group: np.ndarray, n_groups: int) -> np.ndarray:
+    """out[c][g] = sum of V[c][q] over q with group[q] == g (FP64)."""
+    out = np.zeros((V.shape[0], n_groups), dtype=np.complex128)
+    for q in range(V.shape[1]):
+        if 0 <= group[q] < n_groups:
+            out[:, group[q]] += V[:, q]
+    return out

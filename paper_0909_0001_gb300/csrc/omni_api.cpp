@@ -698,6 +698,89 @@ omni_status omni_baselines(const omni_level* levels, int n_levels, int32_t* dm, 
     return OMNI_OK;
 }
 
+omni_status omni_radial_bins(const omni_level* levels, int n_levels, double bin_width, int64_t n_bins,
+                             int32_t* bin_of_lag, int64_t* pairs_per_bin) {
+    if (!(bin_width > 0.0) || !std::isfinite(bin_width) || n_bins < 0)
+        return fail(OMNI_ERR_INVALID_ARG, "bin_width must be > 0 and n_bins >= 0");
+    int64_t N = 0, Q = 0;
+    omni_status st = omni_lattice_shape(levels, n_levels, &N, &Q);
+    if (st != OMNI_OK) return st;
+    std::vector<int64_t> red(Q);
+    std::vector<double> dr(2 * Q);
+    if ((st = omni_baselines(levels, n_levels, nullptr, red.data(), dr.data())) != OMNI_OK) return st;
+    if (pairs_per_bin) std::fill(pairs_per_bin, pairs_per_bin + n_bins, 0);
+    for (int64_t q = 0; q < Q; ++q) {
+        const double len = std::hypot(dr[2 * q], dr[2 * q + 1]);
+        const double b = std::floor(len / bin_width);
+        const int64_t bi = b < (double)n_bins ? (int64_t)b : -1;
+        if (bin_of_lag) bin_of_lag[q] = (int32_t)bi;
+        if (bi >= 0 && pairs_per_bin) pairs_per_bin[bi] += red[q];
+    }
+    return OMNI_OK;
+}
+
+omni_status omni_unique_baselines(const omni_level* levels, int n_levels, int64_t* n_unique,
+                                  int32_t* group_of_lag, double* dr_unique, int64_t* pairs_unique) {
+    if (!n_unique) return fail(OMNI_ERR_INVALID_ARG, "n_unique is NULL");
+    int64_t N = 0, Q = 0;
+    omni_status st = omni_lattice_shape(levels, n_levels, &N, &Q);
+    if (st != OMNI_OK) return st;
+    if (Q > INT32_MAX) return fail(OMNI_ERR_UNSUPPORTED, "too many lags for int32 group indices");
+    std::vector<int64_t> red(Q);
+    std::vector<double> dr(2 * Q);
+    if ((st = omni_baselines(levels, n_levels, nullptr, red.data(), dr.data())) != OMNI_OK) return st;
+    double rmax = 0.0;
+    for (int64_t q = 0; q < Q; ++q) rmax = std::max(rmax, std::hypot(dr[2 * q], dr[2 * q + 1]));
+    const double tol = 1e-9 * rmax;
+    const double cell = tol > 0.0 ? tol : 1.0;
+    // spatial hash of group representatives; each lag looks in the 3x3 cells around it
+    struct Key {
+        int64_t x, y;
+        bool operator==(const Key& o) const { return x == o.x && y == o.y; }
+    };
+    struct KeyHash {
+        size_t operator()(const Key& k) const {
+            return std::hash<int64_t>()(k.x * 0x9E3779B97F4A7C15ULL ^ (uint64_t)k.y);
+        }
+    };
+    std::unordered_map<Key, std::vector<int64_t>, KeyHash> grid;
+    std::vector<double> rep;  // [group][2]
+    std::vector<int64_t> pairs;
+    for (int64_t q = 0; q < Q; ++q) {
+        const double x = dr[2 * q], y = dr[2 * q + 1];
+        const Key k{(int64_t)std::floor(x / cell), (int64_t)std::floor(y / cell)};
+        int64_t found = -1;
+        for (int64_t dx = -1; dx <= 1 && found < 0; ++dx)
+            for (int64_t dy = -1; dy <= 1 && found < 0; ++dy) {
+                auto it = grid.find(Key{k.x + dx, k.y + dy});
+                if (it == grid.end()) continue;
+                for (int64_t gi : it->second)
+                    if (std::hypot(x - rep[2 * gi], y - rep[2 * gi + 1]) <= tol) {
+                        found = gi;
+                        break;
+                    }
+            }
+        if (found < 0) {
+            found = (int64_t)pairs.size();
+            rep.push_back(x);
+            rep.push_back(y);
+            pairs.push_back(0);
+            grid[k].push_back(found);
+        }
+        pairs[found] += red[q];
+        if (group_of_lag) group_of_lag[q] = (int32_t)found;
+    }
+    *n_unique = (int64_t)pairs.size();
+    for (size_t gi = 0; gi < pairs.size(); ++gi) {
+        if (dr_unique) {
+            dr_unique[2 * gi] = rep[2 * gi];
+            dr_unique[2 * gi + 1] = rep[2 * gi + 1];
+        }
+        if (pairs_unique) pairs_unique[gi] = pairs[gi];
+    }
+    return OMNI_OK;
+}
+
 omni_status omni_plan_create(const omni_level* levels, int n_levels, int64_t n_channels,
                              omni_dtype dtype, omni_precision precision, omni_plan** out) {
     if (!out) return fail(OMNI_ERR_INVALID_ARG, "out is NULL");

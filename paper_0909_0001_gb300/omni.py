@@ -32,7 +32,8 @@ EXPORTS = (
     "omni_plan_info", "omni_correlate", "omni_correlate_host", "omni_visibilities",
     "omni_visibilities_host", "omni_reset", "omni_sync", "omni_last_error",
     "omni_status_string", "omni_profile_enable", "omni_profile_read", "omni_correlate_noalloc",
-    "omni_plan_create_batch", "omni_batch_info",
+    "omni_plan_create_batch", "omni_batch_info", "omni_radial_bins", "omni_unique_baselines",
+    "omni_sum_groups",
 )
 
 
@@ -86,6 +87,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "omni_plan_create_batch": (ctypes.c_int, [P(lv), P(ctypes.c_int), ctypes.c_int, i64,
                                                   ctypes.c_int, ctypes.c_int, P(vp)]),
         "omni_batch_info": (ctypes.c_int, [vp, P(ctypes.c_int), P(i64), P(i64)]),
+        "omni_radial_bins": (ctypes.c_int, [lv, ctypes.c_int, dbl, i64, P(i32), P(i64)]),
+        "omni_unique_baselines": (ctypes.c_int, [lv, ctypes.c_int, P(i64), P(i32), P(dbl), P(i64)]),
+        "omni_sum_groups": (ctypes.c_int, [vp, i64, i64, vp, i64, vp, vp]),
         "omni_correlate_noalloc": (ctypes.c_int, [lv, ctypes.c_int, i64, ctypes.c_int, vp, i64,
                                                   vp, vp]),
         "omni_profile_read": (ctypes.c_int, [vp, P(omni_kernel_stat), ctypes.c_int,
@@ -133,6 +137,47 @@ def baselines(levels: Sequence[Level]) -> Tuple[np.ndarray, np.ndarray, np.ndarr
         red.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
         dr.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
     return dm, red, dr
+
+
+def radial_bins(levels: Sequence[Level], bin_width: float, n_bins: int):
+    """(bin_of_lag [Q] int32, -1 beyond the last bin; pairs_per_bin [n_bins] int64), host only."""
+    _, Q = lattice_shape(levels)
+    bins = np.zeros(Q, dtype=np.int32)
+    pairs = np.zeros(max(n_bins, 1), dtype=np.int64)
+    _check(load().omni_radial_bins(_levels(levels), len(levels), float(bin_width), int(n_bins),
+                                   bins.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                   pairs.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+    return bins, pairs[:n_bins]
+
+
+def unique_baselines(levels: Sequence[Level]):
+    """(group_of_lag [Q] int32, dr_unique [G][2], pairs_unique [G] int64), host only."""
+    _, Q = lattice_shape(levels)
+    n = ctypes.c_int64()
+    group = np.zeros(Q, dtype=np.int32)
+    dr = np.zeros((Q, 2))
+    pairs = np.zeros(Q, dtype=np.int64)
+    _check(load().omni_unique_baselines(_levels(levels), len(levels), ctypes.byref(n),
+                                        group.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                        dr.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                        pairs.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+    return group, dr[:n.value], pairs[:n.value]
+
+
+def sum_groups(vis: torch.Tensor, groups: torch.Tensor, n_groups: int,
+               out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """out[c][g] = sum of vis[c][q] over q with groups[q] == g, on the GPU."""
+    if vis.dtype != torch.complex128 or not vis.is_cuda or not vis.is_contiguous() or vis.dim() != 2:
+        raise ValueError("vis must be a contiguous complex128 CUDA tensor [C][Q]")
+    if groups.dtype != torch.int32 or not groups.is_cuda or groups.numel() != vis.shape[1]:
+        raise ValueError("groups must be an int32 CUDA tensor of Q entries")
+    C, Q = vis.shape
+    if out is None:
+        out = torch.empty((C, n_groups), dtype=torch.complex128, device=vis.device)
+    _check(load().omni_sum_groups(ctypes.c_void_p(vis.data_ptr()), C, Q,
+                                  ctypes.c_void_p(groups.contiguous().data_ptr()), int(n_groups),
+                                  ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+    return out
 
 
 def correlate_noalloc(levels: Sequence[Level], volts: torch.Tensor, dtype: str,

@@ -109,3 +109,33 @@ def test_plan_create_rejects_bad_arguments_without_touching_the_gpu(lib):
     assert lib.omni_plan_create(lv, 1, 1, 0, 0, None) == 1                  # no out pointer
     assert lib.omni_correlate(None, None, 1, None) == 1
     assert lib.omni_visibilities(None, None, 1, None) == 1
+
+
+@pytest.mark.parametrize("name", ["three_level", "interleaved", "blocks"])
+def test_radial_bins_match_oracle(lib, name):
+    levels = synth.paper_fixture(name)
+    for w, nb in ((1.0, 40), (7.5, 12)):
+        b, pairs = omni.radial_bins(levels, w, nb)
+        ob, opairs = oracle.radial_bins(levels, w, nb)
+        np.testing.assert_array_equal(b, ob)
+        np.testing.assert_array_equal(pairs, opairs)
+
+
+@pytest.mark.parametrize("levels", [
+    [synth.Level(4, 1, (2.0, 0.0, 0.0, 1.0)), synth.Level(2, 1, (5.0, 0.0, 0.0, 1.0))],
+    synth.paper_fixture("interleaved"),
+    synth.hierarchy([(3, 2), (2, 3)], [0.4, 2.0], [0.2, -0.1]),
+    synth.paper_fixture("warmup_2level"),
+])
+def test_unique_baselines_match_oracle(lib, levels):
+    g, dr, pairs = omni.unique_baselines(levels)
+    og, odr, opairs = oracle.unique_baselines(levels)
+    np.testing.assert_array_equal(g, og)
+    np.testing.assert_allclose(dr, odr, rtol=0, atol=1e-9)
+    np.testing.assert_array_equal(pairs, opairs)
+
+
+def test_epilogue_rejects_bad_arguments(lib):
+    with pytest.raises(omni.OmniError):
+        omni.radial_bins([synth.Level(4, 4)], 0.0, 10)
+    assert lib.omni_sum_groups(None, 1, 1, None, 1, None, None) == 1

@@ -271,3 +271,52 @@ def test_collision_check():
     # a_1 = (1,0) with 4 points and a_2 = (2,0) with 2 points put two antennas at x = 2, 3
     clash = [synth.Level(4, 1, (1.0, 0.0, 0.0, 1.0)), synth.Level(2, 1, (2.0, 0.0, 0.0, 1.0))]
     assert oracle.collides(clash)
+
+
+# ---------------------------------------------------------------- physical baselines
+
+def _pair_separations(levels):
+    r = synth.antenna_positions(levels)
+    return (r[:, None, :] - r[None, :, :]).reshape(-1, 2)
+
+
+def test_radial_profile_of_ones_is_the_pair_distance_histogram():
+    """Sec. III: binning d = l * l^- radially gives the 1-D baseline distribution."""
+    levels = synth.paper_fixture("three_level")
+    w, nb = 5.0, 30
+    _, pairs = oracle.radial_bins(levels, w, nb)
+    d = np.hypot(*_pair_separations(levels).T)
+    hist = np.bincount(np.floor(d / w).astype(int), minlength=nb)[:nb]
+    np.testing.assert_array_equal(pairs, hist)
+
+
+COINCIDENT = [synth.Level(4, 1, (2.0, 0.0, 0.0, 1.0)), synth.Level(2, 1, (5.0, 0.0, 0.0, 1.0))]
+
+
+def test_unique_baselines_match_pair_enumeration():
+    """x = 0,2,4,6 and +5: the lags (3,-1) and (-2,1) both mean a separation of 1."""
+    assert not oracle.collides(COINCIDENT)
+    group, reps, pairs = oracle.unique_baselines(COINCIDENT)
+    sep = np.round(_pair_separations(COINCIDENT), 9)
+    uniq, counts = np.unique(sep, axis=0, return_counts=True)
+    assert len(reps) == len(uniq) < len(group)
+    order = np.lexsort((reps[:, 1], reps[:, 0]))
+    np.testing.assert_allclose(reps[order], uniq)
+    np.testing.assert_array_equal(pairs[order], counts)
+
+
+def test_group_sum_of_correlation_equals_pairs_by_physical_separation():
+    group, reps, _ = oracle.unique_baselines(COINCIDENT)
+    x = synth.random_complex(synth.lattice_dims(COINCIDENT), 1, 2, seed=4)
+    V = oracle.correlate(synth.lattice_dims(COINCIDENT), x)
+    merged = oracle.group_sum(V, group, len(reps))
+    xc = x.numpy().astype(np.float64)
+    xc = xc[..., 0] + 1j * xc[..., 1]
+    r = synth.antenna_positions(COINCIDENT)
+    expect = np.zeros(len(reps), dtype=complex)
+    for t in range(xc.shape[1]):
+        for i in range(len(r)):
+            for j in range(len(r)):
+                g = int(np.argmin(np.hypot(*(reps - (r[i] - r[j])).T)))
+                expect[g] += xc[0, t, i] * np.conj(xc[0, t, j])
+    np.testing.assert_allclose(merged[0], expect, rtol=0, atol=1e-10)
