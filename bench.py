@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--samples", type=int, default=None,
                     help="run a smaller case of the workload (profiling)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-direct", action="store_true", help="skip the direct N^2 context run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -235,6 +236,57 @@ def oracle_rate(w, x_host, target_s=15.0, max_samples=64):
     return units / dt, cores, f"channel 0, first {ts} samples ({units} antenna-samples), {dt:.1f} s"
 
 
+# ------------------------------------------------------------------ direct N^2 context
+
+def direct_n2(w, x_chan, vis_chan):
+    """The N^2 correlator the hypercube avoids, for context: for one channel,
+    V_ij = sum_t x_t(i) conj(x_t(j)) as two real TF32 tensor-core GEMMs
+    (int8 voltages are exact in TF32), then summed per 2n-D lag.  The lag index
+    is linear in the lattice index, q(i, j) = a_i - a_j + const.  Returns
+    (antenna-samples/s, relative difference from the hypercube's visibilities)."""
+    import torch
+    dims = w.dims
+    T = x_chan.shape[0]
+    strides, s = [], 1
+    for n in dims:
+        strides.append(s)
+        s *= 2 * n - 1
+    m = torch.from_numpy(synth_indices(w)).to(x_chan.device)          # [N][D]
+    a = (m * torch.tensor(strides, device=m.device)).sum(dim=1)        # [N]
+    const = sum((n - 1) * st for n, st in zip(dims, strides))
+    q = (a[:, None] - a[None, :] + const).reshape(-1)                  # [N*N]
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = True
+    try:
+        def run():
+            xf = x_chan.float()                                        # [T][N][2]
+            xr, xi = xf[..., 0], xf[..., 1]
+            top = torch.cat([xr, xi], dim=0)                           # [2T][N]
+            vr = top.t() @ top                                         # Xr'Xr + Xi'Xi
+            vi = torch.cat([xi, -xr], dim=0).t() @ top                 # Xi'Xr - Xr'Xi
+            out = torch.zeros(2, s, dtype=torch.float64, device=x_chan.device)
+            out[0].index_add_(0, q, vr.reshape(-1).double())
+            out[1].index_add_(0, q, vi.reshape(-1).double())
+            return torch.complex(out[0], out[1])
+        run()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        v = run()
+        e1.record()
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) * 1e-3
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+    diff = float((v - vis_chan).abs().norm() / vis_chan.abs().norm())
+    return w.n_antennas * T / sec, diff, sec
+
+
+def synth_indices(w):
+    from paper_0909_0001_gb300 import synth
+    return synth.antenna_indices(w.levels).astype("int64")
+
+
 # ------------------------------------------------------------------ arms
 
 def run_reference(args):
@@ -379,6 +431,13 @@ def run_ours(args):
                "ms_per_step": e2e_s * 1e3, "steps": n_e2e}
         del xh, vh
 
+    n2 = None
+    if rank == 0 and not args.no_direct and w.n_antennas <= 16384:
+        # one channel of the same step's voltages (its visibilities are vis[0])
+        rate_n2, diff_n2, sec_n2 = direct_n2(w, x[0], vis[0])
+        n2 = {"value": rate_n2, "unit": UNIT, "seconds": sec_n2, "rel_diff_vs_hypercube": diff_n2,
+              "sample": f"channel 0, {w.samples} samples, TF32 tensor-core GEMMs + lag binning"}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         r, cores, sample = oracle_rate(w, x[0:1, 0:64].cpu())
@@ -397,7 +456,7 @@ def run_ours(args):
                 "roofline": roofline(stats, args.workload, args.precision),
                 "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": sum(s["launches"] for s in stats),
-                "clocks": clocks, "epilogue": epilogue,
+                "clocks": clocks, "epilogue": epilogue, "direct_n2": n2,
                 "kernels": [{k: s[k] for k in ("name", "launches", "total_ms")}
                             for s in stats if s["launches"]]}
         if "fp32" in results and args.precision != "fp32":

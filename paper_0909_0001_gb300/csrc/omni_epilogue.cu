@@ -8,7 +8,7 @@
 // coincident baselines: nearly one group per lag) the sums go straight to
 // global memory.
 #include "omni.h"
-#include "omni_internal.h"
+#include "omni_fft_common.cuh"
 
 #include <algorithm>
 
@@ -85,7 +85,7 @@ extern "C" omni_status omni_sum_groups(const double* vis_dev, int64_t C, int64_t
             const int64_t per_cta = std::max<int64_t>(8 * kSumThreads, (Q + 63) / 64);
             const int64_t ctas = (Q + per_cta - 1) / per_cta;
             const size_t smem = (size_t)n_groups * sizeof(double2);
-            e = cudaFuncSetAttribute(sum_groups_shared, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            e = smem_limit_once((const void*)sum_groups_shared, smem);
             if (e == cudaSuccess && C <= 65535) {
                 sum_groups_shared<<<dim3((unsigned)ctas, (unsigned)C), kSumThreads, smem, s>>>(
                     v, Q, group_dev, n_groups, o, per_cta);

@@ -7,6 +7,8 @@
 #include "omni_internal.h"
 
 #include <cmath>
+#include <mutex>
+#include <utility>
 #include <vector>
 
 namespace omni {
@@ -32,6 +34,22 @@ static __device__ float2 g_tw4096[kTwiddleN];
     cudaError_t e = cudaMemcpyToSymbol(c_tw64, t64.data(), sizeof(float2) * 64);
     if (e != cudaSuccess) return e;
     return cudaMemcpyToSymbol(g_tw4096, t4096.data(), sizeof(float2) * kTwiddleN);
+}
+
+// Raise a kernel's dynamic shared-memory limit once per (kernel, device, size):
+// later launches (including ones recorded into a CUDA graph) make no attribute call.
+inline cudaError_t smem_limit_once(const void* kernel, size_t bytes) {
+    static std::mutex mu;
+    static std::vector<std::pair<std::pair<const void*, int>, size_t>> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    for (auto& d : done)
+        if (d.first.first == kernel && d.first.second == dev && d.second >= bytes) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) done.push_back({{kernel, dev}, bytes});
+    return e;
 }
 
 // ---------------------------------------------------------------- complex helpers

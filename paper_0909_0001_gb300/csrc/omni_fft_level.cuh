@@ -302,14 +302,14 @@ cudaError_t launch_level_t(const Pass& p, const PassArgs& a, cudaStream_t st) {
             const int64_t groups = a.S * p.outer / T::U;
             const int64_t grid = std::min<int64_t>(groups, p.grid_cap);
             auto ks = level_finest_stream<L, SRC>;
-            cudaError_t e = cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::SMEM);
+            cudaError_t e = smem_limit_once((const void*)ks, T::SMEM);
             if (e != cudaSuccess) return e;
             ks<<<(unsigned)grid, T::THREADS, T::SMEM, st>>>(p, a);
             return cudaGetLastError();
         }
     }
     auto k = level_pass<L, FINEST, MODE, SRC>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::SMEM);
+    cudaError_t e = smem_limit_once((const void*)k, T::SMEM);
     if (e != cudaSuccess) return e;
     k<<<(unsigned)blocks, T::THREADS, T::SMEM, st>>>(p, a);
     return cudaGetLastError();
@@ -339,7 +339,7 @@ cudaError_t level_stream_blocks_per_sm(int src_kind, int* out) {
     else return dispatch_src<MODE_MID>(src_kind, [&](auto S) -> cudaError_t {
         using T = LevelTile<L, true, MODE_MID>;
         auto k = level_finest_stream<L, decltype(S)::value>;
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::SMEM);
+        cudaError_t e = smem_limit_once((const void*)k, T::SMEM);
         if (e != cudaSuccess) return e;
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k, T::THREADS, T::SMEM);
     });
@@ -353,13 +353,13 @@ cudaError_t level_last_blocks_per_sm(bool finest, int src_kind, int* out) {
         if (finest) {
             using T = LevelTile<L, true, MODE_LAST>;
             auto k = level_pass<L, true, MODE_LAST, SRC>;
-            cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::SMEM);
+            cudaError_t e = smem_limit_once((const void*)k, T::SMEM);
             if (e != cudaSuccess) return e;
             return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k, T::THREADS, T::SMEM);
         }
         using T = LevelTile<L, false, MODE_LAST>;
         auto k = level_pass<L, false, MODE_LAST, SRC>;
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::SMEM);
+        cudaError_t e = smem_limit_once((const void*)k, T::SMEM);
         if (e != cudaSuccess) return e;
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k, T::THREADS, T::SMEM);
     });

@@ -135,7 +135,7 @@ cudaError_t launch_smem_t(const Pass& p, const PassArgs& a, cudaStream_t st) {
     const int threads = p.W * L1;
     const size_t smem = (size_t)p.W * (L1 * (L2 + 1) + 1) * sizeof(float2);
     auto k = pass_smem<L1, L2, MODE, SRC>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = smem_limit_once((const void*)k, smem);
     if (e != cudaSuccess) return e;
     k<<<(unsigned)blocks, threads, smem, st>>>(p, a);
     return cudaGetLastError();

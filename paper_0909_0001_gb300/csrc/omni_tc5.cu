@@ -349,7 +349,7 @@ cudaError_t upload_tc5_tables() {
 }
 
 cudaError_t tc5_occupancy(int* blocks_per_sm) {
-    cudaError_t e = cudaFuncSetAttribute(tc5_stage_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kT5Smem);
+    cudaError_t e = smem_limit_once((const void*)tc5_stage_b, kT5Smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, tc5_stage_b, kT5Threads, kT5Smem);
 }
@@ -358,7 +358,7 @@ cudaError_t launch_tc5(const Pass& p, const PassArgs& a, cudaStream_t st) {
     if (a.src_kind != SRC_BUF || p.inner % kT5Tile || !a.err) return cudaErrorInvalidValue;
     const int64_t blocks = a.S * (p.inner / kT5Tile);
     if (blocks <= 0) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(tc5_stage_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kT5Smem);
+    cudaError_t e = smem_limit_once((const void*)tc5_stage_b, kT5Smem);
     if (e != cudaSuccess) return e;
     tc5_stage_b<<<(unsigned)blocks, kT5Threads, kT5Smem, st>>>(p, a);
     return cudaGetLastError();

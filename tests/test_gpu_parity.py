@@ -332,3 +332,22 @@ def test_expired_tensor_core_wait_is_reported(monkeypatch):
     monkeypatch.delenv("OMNI_TEST_FORCE_TIMEOUT")
     V = gpu_vis(w.levels, x.cpu(), dtype="ci8", precision="mixed")
     assert np.isfinite(V).all()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "mixed"])
+def test_correlate_replays_from_a_cuda_graph(precision):
+    """omni_correlate (both streams of the overlapped passes) can be captured once
+    and replayed: two replays accumulate twice one call's |F|^2."""
+    w = synth.workload("hier2")
+    x = synth.voltages(w, channels=2, samples=30).cuda()
+    with omni.Plan(w.levels, 2, dtype="ci8", precision=precision) as plan:
+        plan.correlate(x)
+        once = plan.visibilities(reset=True).cpu().numpy()
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            plan.correlate(x)
+        graph.replay()
+        graph.replay()
+        twice = plan.visibilities(reset=True).cpu().numpy()
+    assert relerr_per_channel(twice, 2 * once) <= 1e-6
