@@ -188,6 +188,14 @@ struct omni_plan {
     cudaEvent_t mid_done[2] = {nullptr, nullptr};
     cudaEvent_t last_done[2] = {nullptr, nullptr};
     cudaEvent_t start_ev = nullptr;
+    // mixed plans: part of each chunk's channels go through the FP32 last pass on
+    // split_stream, concurrently with the tensor-core last pass (CUDA cores and
+    // tensor cores busy at once)
+    bool split = false;
+    double split_tc = 1.0;          // fraction of a chunk's channels on tensor cores
+    Pass split_pass{};
+    cudaStream_t split_stream = nullptr;
+    cudaEvent_t split_done[2] = {nullptr, nullptr};
     double2* vis_tmp = nullptr;  // device staging for omni_visibilities_host
     // statistics per pass: forward passes first, then inverse passes
     std::vector<omni_kernel_stat> stats;
@@ -400,6 +408,8 @@ void choose_chunks(omni_plan* pl) {
     if (sms <= 0) slots = 304;
     // fill one wave of the last pass: as many channels as the slots hold
     pl->Cc = std::min<int64_t>(pl->C, std::max<int64_t>(1, slots / ctas));
+    if (const char* env = std::getenv("OMNI_CHUNK_CHANNELS"))
+        pl->Cc = std::min<int64_t>(pl->C, std::max<int64_t>(1, std::atoll(env)));
     const int64_t per_sample = std::max<int64_t>(1, pl->fwd_elems) * (int64_t)sizeof(float2);
     const int64_t samples = std::max<int64_t>(1, target / per_sample);
     pl->Tc = std::max<int64_t>(1, std::min<int64_t>(1024, samples / pl->Cc));
@@ -443,6 +453,12 @@ void release(omni_plan* pl) {
         cudaStreamDestroy(pl->aux_stream);
     }
     if (pl->start_ev) cudaEventDestroy(pl->start_ev);
+    if (pl->split_stream) {
+        cudaStreamSynchronize(pl->split_stream);
+        cudaStreamDestroy(pl->split_stream);
+    }
+    for (int b = 0; b < 2; ++b)
+        if (pl->split_done[b]) cudaEventDestroy(pl->split_done[b]);
     for (int b = 0; b < 2; ++b) {
         if (pl->mid_done[b]) cudaEventDestroy(pl->mid_done[b]);
         if (pl->last_done[b]) cudaEventDestroy(pl->last_done[b]);
@@ -477,6 +493,12 @@ void init_stats(omni_plan* pl) {
             st.tensor = (p.kind == KIND_TC_A || p.kind == KIND_TC_B || p.kind == KIND_TC5_B) ? 1 : 0;
             pl->stats.push_back(st);
         }
+    if (pl->split) {  // the FP32 share of a split last pass
+        omni_kernel_stat st{};
+        snprintf(st.name, sizeof st.name, "fwd axis%d+%d level%d last (FP32 share)", pl->split_pass.axis,
+                 pl->split_pass.axis + 1, pl->split_pass.L);
+        pl->stats.push_back(st);
+    }
 }
 
 cudaEvent_t pool_event(omni_plan* pl) {
@@ -595,8 +617,26 @@ omni_status run_chunk(omni_plan* pl, const void* volts, int64_t vc0, int64_t Tsr
         }
         if (slot >= 0 && p.mode == MODE_LAST)
             OMNI_CUDA(cudaStreamWaitEvent(st, pl->mid_done[slot], 0), "cudaStreamWaitEvent");
+        int64_t cc_split = 0;  // channels of this chunk that go through the FP32 last pass
+        if (slot >= 0 && p.mode == MODE_LAST && pl->split && cc > 1) {
+            cc_split = cc - std::max<int64_t>(1, std::min<int64_t>(cc - 1, (int64_t)(cc * pl->split_tc + 0.5)));
+            const int64_t cc_tc = cc - cc_split;
+            PassArgs b = a;
+            b.S = cc_split;
+            b.c0 = c0 + cc_tc;
+            b.src = (const float2*)src + cc_tc * tc * src_stride;
+            b.fold_scale = 256.0;  // the tensor-core first pass scales the spectra by 1/16
+            a.S = cc_tc;
+            OMNI_CUDA(cudaStreamWaitEvent(pl->split_stream, pl->mid_done[slot], 0), "cudaStreamWaitEvent");
+            cudaError_t e2 = launch_counted(pl, (int)(pl->fwd.size() + pl->inv.size()), pl->split_pass, b,
+                                            pl->split_stream);
+            if (e2 != cudaSuccess) return cuda_fail(e2, "forward pass launch");
+            OMNI_CUDA(cudaEventRecord(pl->split_done[slot], pl->split_stream), "cudaEventRecord");
+        }
         cudaError_t e = launch_counted(pl, (int)k, p, a, launch_stream);
         if (e != cudaSuccess) return cuda_fail(e, "forward pass launch");
+        if (cc_split > 0)
+            OMNI_CUDA(cudaStreamWaitEvent(st, pl->split_done[slot], 0), "cudaStreamWaitEvent");
         if (slot >= 0)
             OMNI_CUDA(cudaEventRecord(p.mode == MODE_MID ? pl->mid_done[slot] : pl->last_done[slot],
                                       launch_stream), "cudaEventRecord");
@@ -838,6 +878,34 @@ omni_status omni_plan_create(const omni_level* levels, int n_levels, int64_t n_c
                 return cuda_fail(e, "creating the overlap events");
             }
     }
+    // mixed plans: split each chunk's last pass between tensor cores and CUDA cores
+    if (pl->overlap && pl->precision == OMNI_MIXED_FP16 && pl->fwd.back().kind == KIND_TC_B) {
+        // fraction of a chunk's channels on tensor cores; measured on the 2-level
+        // workload: 1.0 (no split) 23.9 ms, 0.6 23.5, 0.45 23.2, 0.3 23.1 ms per step
+        double frac = 0.3;
+        if (const char* env = std::getenv("OMNI_SPLIT_TC")) frac = std::atof(env);
+        if (frac < 1.0 && frac > 0.0) {
+            const Pass& last = pl->fwd.back();
+            Pass sp{};
+            sp.axis = last.axis;
+            sp.mode = MODE_LAST;
+            sp.L = last.L;
+            sp.n = last.n;
+            sp.q_out = last.q_out;
+            sp.inner = last.inner;
+            sp.outer = 1;
+            choose_level(sp);
+            pl->split_pass = sp;
+            pl->split_tc = frac;
+            if ((e = cudaStreamCreateWithFlags(&pl->split_stream, cudaStreamNonBlocking)) != cudaSuccess ||
+                (e = cudaEventCreateWithFlags(&pl->split_done[0], cudaEventDisableTiming)) != cudaSuccess ||
+                (e = cudaEventCreateWithFlags(&pl->split_done[1], cudaEventDisableTiming)) != cudaSuccess) {
+                release(pl);
+                return cuda_fail(e, "creating the split stream");
+            }
+            pl->split = true;
+        }
+    }
     // persistent finest-level passes: one wave of resident CTAs
     for (size_t k = 0; k < pl->fwd.size(); ++k) {
         Pass& p = pl->fwd[k];
@@ -995,6 +1063,8 @@ omni_status omni_correlate(omni_plan* pl, const void* volts_dev, int64_t T, void
         // the aux stream starts after everything already queued on the caller's stream
         OMNI_CUDA(cudaEventRecord(pl->start_ev, s), "cudaEventRecord");
         OMNI_CUDA(cudaStreamWaitEvent(pl->aux_stream, pl->start_ev, 0), "cudaStreamWaitEvent");
+        if (pl->split)
+            OMNI_CUDA(cudaStreamWaitEvent(pl->split_stream, pl->start_ev, 0), "cudaStreamWaitEvent");
         for (int b = 0; b < 2; ++b) OMNI_CUDA(cudaEventRecord(pl->last_done[b], s), "cudaEventRecord");
     }
     int64_t j = 0;

@@ -187,6 +187,7 @@ level_pass(Pass p, PassArgs a) {
             __syncthreads();
         }
         double* P = a.P + (a.c0 + cc) * a.P_stride;
+        const double fs = a.fold_scale != 0.0 ? a.fold_scale : 1.0;
 #pragma unroll
         for (int li = 0; li < LPT; ++li) {
             const int l = threadIdx.x + li * NT;
@@ -195,7 +196,7 @@ level_pass(Pass p, PassArgs a) {
                 if (w < i_lim) {
 #pragma unroll
                     for (int k = 0; k < L; ++k)
-                        P[((int64_t)k * L + ka) * inner + i0 + w] += (double)acc[li][k];
+                        P[((int64_t)k * L + ka) * inner + i0 + w] += fs * (double)acc[li][k];
                 }
             }
         }

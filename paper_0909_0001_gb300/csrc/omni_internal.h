@@ -75,6 +75,7 @@ struct PassArgs {
     double scale;        // INV_LAST: 1/L
     int* err;            // device error word (bounded waits that expired set it to 1)
     int force_expire;    // test hook: make the first bounded wait expire
+    double fold_scale;   // FP32 LAST passes: factor on the FP64 fold (0 means 1)
 };
 
 // Upload the twiddle tables to the current device (once per device).

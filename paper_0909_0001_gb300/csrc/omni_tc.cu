@@ -33,6 +33,7 @@
 #include <algorithm>
 
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -398,10 +399,24 @@ bool tc_supports(const int32_t* n, int D, int dtype_is_ci8) {
     return D == 4 && n[0] == 16 && n[1] == 16 && n[2] == 8 && n[3] == 8 && dtype_is_ci8;
 }
 
+// Dynamic shared memory reserved (unused) by each stage-B CTA so that only one
+// fits per SM, leaving registers for stage-A CTAs of the next chunk to run
+// beside it (OMNI_TCB_PER_SM=1); 0 keeps two stage-B CTAs per SM.
+size_t stage_b_pad() {
+    static const size_t pad = [] {
+        const char* env = std::getenv("OMNI_TCB_PER_SM");
+        return (env && std::atoi(env) == 1) ? (size_t)100 * 1024 : (size_t)0;
+    }();
+    return pad;
+}
+
 cudaError_t tc_occupancy(int kind, int* blocks_per_sm) {
     if (kind == KIND_TC_A)
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, tc_stage_a, kStageAWarps * 32, 0);
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, tc_stage_b, kStageBWarps * 32, 0);
+    cudaError_t e = smem_limit_once((const void*)tc_stage_b, stage_b_pad());
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, tc_stage_b, kStageBWarps * 32,
+                                                         stage_b_pad());
 }
 
 cudaError_t launch_tc(const Pass& p, const PassArgs& a, cudaStream_t st) {
@@ -417,7 +432,12 @@ cudaError_t launch_tc(const Pass& p, const PassArgs& a, cudaStream_t st) {
     if (a.src_kind != SRC_BUF || p.inner % kTileKA) return cudaErrorInvalidValue;
     const int64_t blocks = a.S * (p.inner / kTileKA);
     if (blocks <= 0) return cudaSuccess;
-    tc_stage_b<<<(unsigned)blocks, kStageBWarps * 32, 0, st>>>(p, a);
+    const size_t pad = stage_b_pad();
+    if (pad) {
+        cudaError_t e = smem_limit_once((const void*)tc_stage_b, pad);
+        if (e != cudaSuccess) return e;
+    }
+    tc_stage_b<<<(unsigned)blocks, kStageBWarps * 32, pad, st>>>(p, a);
     return cudaGetLastError();
 }
 

@@ -315,6 +315,23 @@ def test_mixed_tcgen05_variant(monkeypatch):
     assert relerr_per_channel(V, default) <= 1e-6
 
 
+@pytest.mark.parametrize("frac", ["0", "0.3", "0.5", "0.8"])
+def test_mixed_split_last_pass(monkeypatch, frac):
+    """Channels of a chunk split between the tensor-core and the FP32 last pass
+    (run concurrently) give the same visibilities as either alone."""
+    w = synth.workload("hier2")
+    x = synth.voltages(w, channels=11, samples=6)
+    monkeypatch.setenv("OMNI_SPLIT_TC", "0")
+    tc_only = gpu_vis(w.levels, x, dtype="ci8", precision="mixed")
+    monkeypatch.setenv("OMNI_SPLIT_TC", frac)
+    V, _ = check(w.levels, x, dtype="ci8", tol=TOL_MIXED, precision="mixed")
+    assert relerr_per_channel(V, tc_only) <= 2e-5
+    # several chunks, so both stream slots and the split events are reused
+    monkeypatch.setenv("OMNI_CHUNK_MB", "8")
+    V2 = gpu_vis(w.levels, x, dtype="ci8", precision="mixed")
+    assert relerr_per_channel(V2, V) <= 2e-5
+
+
 def test_expired_tensor_core_wait_is_reported(monkeypatch):
     """A bounded device wait that runs out returns OMNI_ERR_TIMEOUT; the context stays usable.
 
