@@ -138,32 +138,54 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ roofline
 
-def kernel_source_hash():
+# kernel sources behind each pass kind (plus the shared headers)
+_PASS_SOURCES = [("tcgen05", ("omni_tc5.cu",)), ("tc", ("omni_tc.cu",)),
+                 ("level", ("omni_fft_level.cuh", "omni_fft_level_a.cu", "omni_fft_level_b.cu")),
+                 ("smem", ("omni_fft_smem.cuh", "omni_fft_smem_a.cu", "omni_fft_smem_b.cu",
+                           "omni_fft_smem_c.cu")),
+                 ("reg", ("omni_fft_reg.cuh", "omni_fft_reg_a.cu", "omni_fft_reg_b.cu")),
+                 ("direct", ("omni_fft_direct.cu",))]
+
+
+def kernel_source_hash(pass_name):
+    """Hash of the sources that define the kernel of a pass (by its stat name)."""
     from paper_0909_0001_gb300.build import CSRC
+    kind = pass_name.split()[2] if len(pass_name.split()) > 2 else ""
+    files = ["omni_fft_common.cuh", "omni_internal.h"]
+    for key, srcs in _PASS_SOURCES:
+        if kind.startswith(key):
+            files += list(srcs)
+            break
     h = hashlib.sha256()
-    for f in sorted(os.listdir(CSRC)):
-        if f.endswith((".cu", ".cuh", ".h", ".cpp")):
-            with open(os.path.join(CSRC, f), "rb") as fh:
+    for f in files:
+        path = os.path.join(CSRC, f)
+        if os.path.exists(path):
+            with open(path, "rb") as fh:
                 h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel_name, workload, precision):
-    """DRAM bytes per launch from a committed ncu summary, if it matches this build."""
+def recorded_traffic(kernel_name, workload, precision, units_per_launch):
+    """DRAM bytes per launch from a committed ncu summary while the kernel's
+    sources match; scaled by the channel-samples per launch when the bench's
+    launches are a different size (the traffic grows in proportion to them)."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
-        return None
-    want = kernel_source_hash()
+        return None, None
+    want = kernel_source_hash(kernel_name)
     with open(path) as f:
         for line in f:
             p = line.strip().split("|")
-            if len(p) >= 5 and p[0].strip() == workload and p[1].strip() == precision \
+            if len(p) >= 6 and p[0].strip() == workload and p[1].strip() == precision \
                     and p[2].strip() == kernel_name and p[3].strip() == want:
                 try:
-                    return float(p[4])
+                    b, u = float(p[4]), float(p[5])
                 except ValueError:
-                    return None
-    return None
+                    return None, None
+                if abs(u - units_per_launch) <= 0.01 * u:
+                    return b, "ncu, same launch size"
+                return b * units_per_launch / u, "ncu at %g channel-samples per launch, scaled" % u
+    return None, None
 
 
 def alu_peak_tflops(sm_mhz):
@@ -171,7 +193,13 @@ def alu_peak_tflops(sm_mhz):
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
-def roofline(stats, workload, path_precision):
+def units_per_launch(stat, profiled_units):
+    """Channel-samples one launch of a forward pass processes (profiled_units:
+    channels x samples over all the profiled steps)."""
+    return profiled_units / max(1, stat["launches"])
+
+
+def roofline(stats, workload, path_precision, profiled_units=0):
     """Roofline of the dominant kernel (largest share of the event-timed region)."""
     timed = [s for s in stats if s["launches"] > 0 and s["total_ms"] > 0]
     if not timed:
@@ -203,7 +231,9 @@ def roofline(stats, workload, path_precision):
         main = {"bound": "alu", "achieved": round(tfs, 2), "peak": round(alu_peak, 1),
                 "unit": "TFLOP/s", "frac": round(tfs / alu_peak, 4),
                 "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 x max SM clock"}
-    main.update({"traffic": recorded_traffic(top["name"], workload, path_precision),
+    traffic, traffic_note = recorded_traffic(top["name"], workload, path_precision,
+                                             units_per_launch(top, profiled_units))
+    main.update({"traffic": traffic, "traffic_note": traffic_note,
                  "kernel": top["name"], "flops_per_launch": flops_per_launch,
                  "avg_launch_ms": avg_s * 1e3,
                  "share_of_kernel_time": round(top["total_ms"] / total, 4),
@@ -453,7 +483,8 @@ def run_ours(args):
                 "config": dict(workload_config(w, args.precision),
                                parallelism=f"{world} ranks x {w.channels} channels"
                                if world > 1 else "single GPU"),
-                "roofline": roofline(stats, args.workload, args.precision),
+                "roofline": roofline(stats, args.workload, args.precision,
+                                     w.channels * w.samples * args.steps),
                 "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": sum(s["launches"] for s in stats),
                 "clocks": clocks, "epilogue": epilogue, "direct_n2": n2,

@@ -22,6 +22,8 @@ using namespace omni;
 
 namespace {
 
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
 thread_local std::string g_last_error;
 
 omni_status fail(omni_status st, const char* fmt, ...) {
@@ -166,6 +168,7 @@ struct omni_plan {
     omni_precision precision = OMNI_FP32;
     std::vector<Pass> fwd, inv;
     int64_t Cc = 1, Tc = 1;   // forward chunk: channels x samples
+    int64_t chunk_mb = 1536;  // target size of each chunk scratch buffer
     int64_t Cv = 1;           // inverse batch: channels
     int64_t fwd_elems = 0;    // float2 per sample, largest non-final forward output
     int64_t inv_elems = 0;    // float2 per channel, largest non-final inverse output
@@ -310,7 +313,7 @@ omni_status build_passes(omni_plan* pl) {
         pb.q_out = g.Lp[2] * g.Lp[3];
         pb.inner = (int64_t)g.Lp[0] * g.Lp[1];
         pb.outer = 1;
-        pb.W = 32;
+        pb.W = pb.kind == KIND_TC_B ? tc_stage_b_tile() : 32;
         pl->fwd.push_back(pa);
         pl->fwd.push_back(pb);
         pl->fwd_elems = pa.outer * pa.q_out;
@@ -377,12 +380,13 @@ omni_status build_passes(omni_plan* pl) {
 }
 
 // Chunk sizes: the last pass gets one wave of resident CTAs (channels x inner
-// tiles), and each scratch buffer holds about OMNI_CHUNK_MB (default 384) MB of
-// samples: long chunks amortise the FP64 fold and the launch ramp better than
-// L2-sized ones (measured on the 2-level workload: 96 MB 33.7 ms, 192 MB
-// 26.6 ms, 384 MB 23.4 ms per step).
+// tiles), and each scratch buffer holds about chunk_mb MB of samples (1536 for
+// a single array, 256 for each member of a batch; OMNI_CHUNK_MB overrides):
+// long chunks amortise the FP64 fold and the launch ramp (measured on the
+// 2-level workload, FP32 path: 96 MB 33.7 ms, 192 MB 26.6, 384 MB 22.6,
+// 768 MB 21.3, 1536 MB 20.8 ms per step).
 void choose_chunks(omni_plan* pl) {
-    int64_t mb = 384;
+    int64_t mb = pl->chunk_mb;
     if (const char* env = std::getenv("OMNI_CHUNK_MB")) mb = std::max<int64_t>(1, std::atoll(env));
     const int64_t target = mb << 20;
     // CTAs the last pass runs per channel of a chunk
@@ -821,8 +825,18 @@ omni_status omni_unique_baselines(const omni_level* levels, int n_levels, int64_
     return OMNI_OK;
 }
 
+static omni_status create_plan(const omni_level* levels, int n_levels, int64_t n_channels,
+                               omni_dtype dtype, omni_precision precision, int64_t chunk_mb,
+                               omni_plan** out);
+
 omni_status omni_plan_create(const omni_level* levels, int n_levels, int64_t n_channels,
                              omni_dtype dtype, omni_precision precision, omni_plan** out) {
+    return create_plan(levels, n_levels, n_channels, dtype, precision, 1536, out);
+}
+
+static omni_status create_plan(const omni_level* levels, int n_levels, int64_t n_channels,
+                               omni_dtype dtype, omni_precision precision, int64_t chunk_mb,
+                               omni_plan** out) {
     if (!out) return fail(OMNI_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (n_channels < 1) return fail(OMNI_ERR_INVALID_ARG, "n_channels must be >= 1");
@@ -861,6 +875,7 @@ omni_status omni_plan_create(const omni_level* levels, int n_levels, int64_t n_c
         release(pl);
         return st;
     }
+    pl->chunk_mb = chunk_mb;
     choose_chunks(pl);
     // overlap the two passes of consecutive chunks (OMNI_OVERLAP=0 turns it off)
     pl->overlap = pl->fwd.size() == 2;
@@ -880,9 +895,10 @@ omni_status omni_plan_create(const omni_level* levels, int n_levels, int64_t n_c
     }
     // mixed plans: split each chunk's last pass between tensor cores and CUDA cores
     if (pl->overlap && pl->precision == OMNI_MIXED_FP16 && pl->fwd.back().kind == KIND_TC_B) {
-        // fraction of a chunk's channels on tensor cores; measured on the 2-level
-        // workload: 1.0 (no split) 23.9 ms, 0.6 23.5, 0.45 23.2, 0.3 23.1 ms per step
-        double frac = 0.3;
+        // fraction of a chunk's channels on tensor cores (off by default: with
+        // 768 MB chunks on the 2-level workload, no split 22.56 ms, 0.6 22.47,
+        // 0.3 24.07 ms per step -- both kernels are issue-limited)
+        double frac = 0.0;
         if (const char* env = std::getenv("OMNI_SPLIT_TC")) frac = std::atof(env);
         if (frac < 1.0 && frac > 0.0) {
             const Pass& last = pl->fwd.back();
@@ -977,8 +993,8 @@ omni_status omni_plan_create_batch(const omni_level* const* levels_per_array,
         int b = a + 1;
         while (b < n_arrays && same_shape(a, b)) ++b;
         omni_plan* sub = nullptr;
-        omni_status st = omni_plan_create(levels_per_array[a], n_levels_per_array[a],
-                                          (int64_t)(b - a) * n_channels, dtype, precision, &sub);
+        omni_status st = create_plan(levels_per_array[a], n_levels_per_array[a],
+                                     (int64_t)(b - a) * n_channels, dtype, precision, 256, &sub);
         if (st != OMNI_OK) {
             release(pl);
             return st;
@@ -1067,11 +1083,14 @@ omni_status omni_correlate(omni_plan* pl, const void* volts_dev, int64_t T, void
             OMNI_CUDA(cudaStreamWaitEvent(pl->split_stream, pl->start_ev, 0), "cudaStreamWaitEvent");
         for (int b = 0; b < 2; ++b) OMNI_CUDA(cudaEventRecord(pl->last_done[b], s), "cudaEventRecord");
     }
+    // equal-sized chunks (no short tail chunk paying a whole fold and launch)
+    const int64_t Cb = ceil_div(pl->C, ceil_div(pl->C, pl->Cc));
+    const int64_t Tb = ceil_div(T, ceil_div(T, pl->Tc));
     int64_t j = 0;
-    for (int64_t c0 = 0; c0 < pl->C; c0 += pl->Cc) {
-        const int64_t cc = std::min(pl->Cc, pl->C - c0);
-        for (int64_t t0 = 0; t0 < T; t0 += pl->Tc, ++j) {
-            const int64_t tc = std::min(pl->Tc, T - t0);
+    for (int64_t c0 = 0; c0 < pl->C; c0 += Cb) {
+        const int64_t cc = std::min(Cb, pl->C - c0);
+        for (int64_t t0 = 0; t0 < T; t0 += Tb, ++j) {
+            const int64_t tc = std::min(Tb, T - t0);
             st = run_chunk(pl, volts_dev, c0, T, t0, c0, cc, tc, s, pl->overlap ? (int)(j & 1) : -1);
             if (st != OMNI_OK) return st;
         }
@@ -1121,11 +1140,14 @@ omni_status omni_correlate_host(omni_plan* pl, const void* volts_host, int64_t T
     // staging buffer of chunk j-2 ('freed'); compute waits for 'ready'.
     OMNI_CUDA(cudaEventRecord(pl->freed[0], s), "cudaEventRecord");
     OMNI_CUDA(cudaEventRecord(pl->freed[1], s), "cudaEventRecord");
+    // equal-sized chunks (no short tail chunk paying a whole fold and launch)
+    const int64_t Cb = ceil_div(pl->C, ceil_div(pl->C, pl->Cc));
+    const int64_t Tb = ceil_div(T, ceil_div(T, pl->Tc));
     int64_t j = 0;
-    for (int64_t c0 = 0; c0 < pl->C; c0 += pl->Cc) {
-        const int64_t cc = std::min(pl->Cc, pl->C - c0);
-        for (int64_t t0 = 0; t0 < T; t0 += pl->Tc, ++j) {
-            const int64_t tc = std::min(pl->Tc, T - t0);
+    for (int64_t c0 = 0; c0 < pl->C; c0 += Cb) {
+        const int64_t cc = std::min(Cb, pl->C - c0);
+        for (int64_t t0 = 0; t0 < T; t0 += Tb, ++j) {
+            const int64_t tc = std::min(Tb, T - t0);
             const int b = (int)(j & 1);
             OMNI_CUDA(cudaStreamWaitEvent(pl->copy_stream, pl->freed[b], 0), "cudaStreamWaitEvent");
             for (int64_t k = 0; k < cc; ++k) {

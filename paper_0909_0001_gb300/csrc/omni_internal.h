@@ -94,6 +94,7 @@ cudaError_t level_stream_occupancy(const Pass& p, int src_kind, int* blocks_per_
 bool tc_supports(const int32_t* n, int D, int dtype_is_ci8);
 cudaError_t upload_tc_tables();
 cudaError_t tc_occupancy(int kind, int* blocks_per_sm);
+int tc_stage_b_tile();  // level-1 frequencies per stage-B CTA
 cudaError_t launch_tc(const Pass& p, const PassArgs& a, cudaStream_t stream);
 cudaError_t upload_tc5_tables();
 cudaError_t tc5_occupancy(int* blocks_per_sm);

@@ -49,9 +49,6 @@ __device__ uint2 g_tcB4[4][2][32];     // [nt][hl][lane]     stage B GEMM 4, B o
 constexpr float kScaleA = 1.0f / 16.0f;   // stage A output scale
 constexpr double kFoldB = 256.0;          // (1/kScaleA)^2 applied at the FP64 fold
 constexpr int kStageAWarps = 8;
-constexpr int kStageBWarps = 8;
-constexpr int kTileKA = 32;               // level-1 frequencies per stage-B CTA
-constexpr int kPitchB = 65;               // shared row pitch (blocks) per kA, odd
 
 __device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
     // not volatile: the product has no side effects, so the compiler may
@@ -181,73 +178,73 @@ __global__ void __launch_bounds__(kStageAWarps * 32) tc_stage_a(Pass p, PassArgs
 
 // ------------------------------------------------------------------ stage B (LAST)
 
-// CTA = (channel of the chunk, tile of 32 level-1 frequencies kA); 8 warps,
-// 4 kA each; the next sample's tile is loaded into registers while the
-// current one is transformed.
-__global__ void __launch_bounds__(kStageBWarps * 32, 2) tc_stage_b(Pass p, PassArgs a) {
-    constexpr int KPW = kTileKA / kStageBWarps;  // kA per warp
-    constexpr int TILE = 64 * kTileKA;           // complex values per sample tile
-    constexpr int F4 = TILE / 2 / (kStageBWarps * 32);  // float4 loads per thread
-    constexpr size_t TILE_BYTES = sizeof(float2) * kTileKA * kPitchB;
-    constexpr size_t FOLD_BYTES = sizeof(float) * kStageBWarps * KPW * 8 * 32;
-    // the sample tile and, after the last sample, the fold staging share one buffer
-    __shared__ __align__(16) unsigned char smem[TILE_BYTES > FOLD_BYTES ? TILE_BYTES : FOLD_BYTES];
-    float2* sz = reinterpret_cast<float2*>(smem);
-    auto sfold = reinterpret_cast<float (*)[KPW][8][32]>(smem);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
-    const int64_t tiles = p.inner / kTileKA;             // 1024 / 32
-    const int64_t cc = blockIdx.x / tiles;
-    const int64_t kA0 = (blockIdx.x - cc * tiles) * kTileKA;
-    // constant fragments in registers
-    uint32_t a3[2][2][4], b4[4][2][2];
+// A warp owns (channel of the chunk, 4 consecutive level-1 frequencies kA) for
+// all of the chunk's samples.  Each lane loads its two blocks' 4-kA runs (32
+// bytes each, whole sectors) straight from global memory: no shared-memory
+// tile and no block-wide barrier.  (A tiled form with 32 kA per CTA staged
+// through shared memory, and forms with two or four kA interleaved per warp or
+// with register prefetch of the next sample, all measured within 6% of this
+// one: the legacy HMMA pipe, 57% busy, is the limit, not latency.)
+constexpr int kB2Warps = 4;
+constexpr int kB2KPW = 4;  // kA per warp
+
+template <bool PREFETCH>
+__global__ void __launch_bounds__(kB2Warps * 32, 4) tc_stage_b(Pass p, PassArgs a) {
+    __shared__ uint4 sA3[2][2][32];
+    __shared__ uint2 sB4[4][2][32];
+    for (int i = threadIdx.x; i < 2 * 2 * 32; i += blockDim.x) (&sA3[0][0][0])[i] = (&g_tcA3[0][0][0])[i];
+    for (int i = threadIdx.x; i < 4 * 2 * 32; i += blockDim.x) (&sB4[0][0][0])[i] = (&g_tcB4[0][0][0])[i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const int64_t groups = p.inner / kB2KPW;
+    const int64_t u = (int64_t)blockIdx.x * kB2Warps + (threadIdx.x >> 5);
+    if (u >= a.S * groups) return;
+    const int64_t cc = u / groups;
+    const int64_t kA0 = (u - cc * groups) * kB2KPW;
+    // GEMM 4 fragments: in registers, or (PREFETCH) read from shared memory at
+    // each use so that the registers hold the next sample's data instead
+    uint32_t b4[4][2][2];
+    if (!PREFETCH)
 #pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
+        for (int nt = 0; nt < 4; ++nt)
 #pragma unroll
-        for (int hl = 0; hl < 2; ++hl) {
-            const uint4 w = g_tcA3[mt][hl][lane];
-            a3[mt][hl][0] = w.x; a3[mt][hl][1] = w.y; a3[mt][hl][2] = w.z; a3[mt][hl][3] = w.w;
-        }
+            for (int hl = 0; hl < 2; ++hl) {
+                const uint2 w = sB4[nt][hl][lane];
+                b4[nt][hl][0] = w.x;
+                b4[nt][hl][1] = w.y;
+            }
+    float acc[kB2KPW][8];
 #pragma unroll
-    for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-        for (int hl = 0; hl < 2; ++hl) {
-            const uint2 w = g_tcB4[nt][hl][lane];
-            b4[nt][hl][0] = w.x; b4[nt][hl][1] = w.y;
-        }
-    float acc[KPW][8];
-#pragma unroll
-    for (int q = 0; q < KPW; ++q)
+    for (int q = 0; q < kB2KPW; ++q)
 #pragma unroll
         for (int r = 0; r < 8; ++r) acc[q][r] = 0.f;
-
-    // load slot q of thread: block b = e / 16, kA pair j = e % 16 (float4 = kA 2j, 2j+1)
-    float4 pre[F4];
-    auto fetch = [&](int64_t s) {
-        const float4* base = reinterpret_cast<const float4*>(a.src) +
-                             (src_base(a, s) + kA0) / 2;
-#pragma unroll
-        for (int q = 0; q < F4; ++q) {
-            const int e = threadIdx.x + q * kStageBWarps * 32;
-            const int b = e >> 4, j = e & 15;
-            pre[q] = base[(int64_t)b * (p.inner / 2) + j];
-        }
+    // blocks m3 + 8 m4 with m4 = g, m3 = 2t and 2t + 1; 4 kA each (two float4)
+    const int64_t b0 = 8 * g + 2 * t;
+    const int64_t step = p.inner / 2;  // one block, in float4
+    auto fetch = [&](float4 (&z)[4], int64_t s) {
+        const float4* base = reinterpret_cast<const float4*>(
+            reinterpret_cast<const float2*>(a.src) + src_base(a, s) + b0 * p.inner + kA0);
+        z[0] = __ldg(base);
+        z[1] = __ldg(base + 1);
+        z[2] = __ldg(base + step);
+        z[3] = __ldg(base + step + 1);
     };
-    fetch(cc * a.tc);
+    float4 cur[4], nxt[4];
+    if (PREFETCH) fetch(nxt, cc * a.tc);
     for (int ts = 0; ts < a.tc; ++ts) {
+        if (PREFETCH) {
 #pragma unroll
-        for (int q = 0; q < F4; ++q) {
-            const int e = threadIdx.x + q * kStageBWarps * 32;
-            const int b = e >> 4, j = e & 15;
-            sz[(2 * j) * kPitchB + b] = make_float2(pre[q].x, pre[q].y);
-            sz[(2 * j + 1) * kPitchB + b] = make_float2(pre[q].z, pre[q].w);
+            for (int i = 0; i < 4; ++i) cur[i] = nxt[i];
+            if (ts + 1 < a.tc) fetch(nxt, cc * a.tc + ts + 1);
+        } else {
+            fetch(cur, cc * a.tc + ts);
         }
-        if (ts + 1 < a.tc) fetch(cc * a.tc + ts + 1);
-        __syncthreads();
 #pragma unroll
-        for (int q = 0; q < KPW; ++q) {
-            const int kl = warp * KPW + q;
-            const float2 z0 = sz[kl * kPitchB + 8 * g + 2 * t];
-            const float2 z1 = sz[kl * kPitchB + 8 * g + 2 * t + 1];
+        for (int q = 0; q < kB2KPW; ++q) {
+            // kA0 + q of blocks b0 (z0) and b0 + 1 (z1)
+            const float4 h0 = cur[q >> 1], h1 = cur[2 + (q >> 1)];
+            const float2 z0 = (q & 1) ? make_float2(h0.z, h0.w) : make_float2(h0.x, h0.y);
+            const float2 z1 = (q & 1) ? make_float2(h1.z, h1.w) : make_float2(h1.x, h1.y);
             uint32_t bh0, bl0, bh1, bl1;
             split2(z0.x, z1.x, bh0, bl0);  // rows re m3 = 2t, 2t+1
             split2(z0.y, z1.y, bh1, bl1);  // rows im m3
@@ -259,8 +256,12 @@ __global__ void __launch_bounds__(kStageBWarps * 32, 2) tc_stage_b(Pass p, PassA
 #pragma unroll
             for (int term = 0; term < 3; ++term)
 #pragma unroll
-                for (int mt = 0; mt < 2; ++mt)
-                    mma16816(d2[mt], a3[mt][term == 1 ? 1 : 0], term == 2 ? bl0 : bh0, term == 2 ? bl1 : bh1);
+                for (int mt = 0; mt < 2; ++mt) {
+                    const uint4 w = sA3[mt][term == 1 ? 1 : 0][lane];
+                    const uint32_t af[4] = {w.x, w.y, w.z, w.w};
+                    mma16816(d2[mt], af, term == 2 ? bl0 : bh0, term == 2 ? bl1 : bh1);
+                }
+            // chain: the GEMM 3 accumulators are the A fragments of GEMM 4
             uint32_t ah[4], al[4];
             split2(d2[0][0], d2[0][1], ah[0], al[0]);
             split2(d2[0][2], d2[0][3], ah[1], al[1]);
@@ -274,8 +275,19 @@ __global__ void __launch_bounds__(kStageBWarps * 32, 2) tc_stage_b(Pass p, PassA
 #pragma unroll
             for (int term = 0; term < 3; ++term)
 #pragma unroll
-                for (int nt = 0; nt < 4; ++nt)
-                    mma16816(d3[nt], term == 2 ? al : ah, b4[nt][term == 1 ? 1 : 0][0], b4[nt][term == 1 ? 1 : 0][1]);
+                for (int nt = 0; nt < 4; ++nt) {
+                    uint32_t f0, f1;
+                    if (PREFETCH) {
+                        const uint2 w = sB4[nt][term == 1 ? 1 : 0][lane];
+                        f0 = w.x;
+                        f1 = w.y;
+                    } else {
+                        f0 = b4[nt][term == 1 ? 1 : 0][0];
+                        f1 = b4[nt][term == 1 ? 1 : 0][1];
+                    }
+                    mma16816(d3[nt], term == 2 ? al : ah, f0, f1);
+                }
+            // |F|^2: n-tiles 0, 1 real and 2, 3 imaginary parts of k4 < 8, k4 >= 8
 #pragma unroll
             for (int nt = 0; nt < 2; ++nt)
 #pragma unroll
@@ -283,24 +295,22 @@ __global__ void __launch_bounds__(kStageBWarps * 32, 2) tc_stage_b(Pass p, PassA
                     acc[q][4 * nt + r] = fmaf(d3[nt][r], d3[nt][r],
                                               fmaf(d3[nt + 2][r], d3[nt + 2][r], acc[q][4 * nt + r]));
         }
-        __syncthreads();
     }
-    // fold: via shared memory so that the FP64 updates run along kA (coalesced)
-#pragma unroll
-    for (int q = 0; q < KPW; ++q)
-#pragma unroll
-        for (int r = 0; r < 8; ++r) sfold[warp][q][r][lane] = acc[q][r];
-    __syncthreads();
+    // fold: fragment r = 4 nt + rr holds (k3 = g + 8 [rr >= 2], k4 = 8 nt + 2t + (rr & 1));
+    // the warp's 4 kA are 32 contiguous bytes of each P row (row = 16 k4 + k3)
     double* P = a.P + (a.c0 + cc) * a.P_stride;
-    // thread -> (k4, k3) row, kA column; 256 rows x 32 kA
-    for (int e = threadIdx.x; e < 256 * kTileKA; e += blockDim.x) {
-        const int kl = e % kTileKA, row = e / kTileKA;
-        const int k4 = row / 16, k3 = row % 16;
-        // inverse of the fragment map: k3 = g + 8 (r >= 2 within the n-tile), k4 = 8 nt + 2t + (r & 1)
-        const int nt = k4 / 8, tt = (k4 % 8) / 2, r = (k3 >= 8 ? 2 : 0) + (k4 & 1);
-        const int gg = k3 % 8;
-        const float v = sfold[kl / KPW][kl % KPW][4 * nt + r][4 * gg + tt];
-        P[(int64_t)row * p.inner + kA0 + kl] += kFoldB * (double)v;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        const int nt = r >> 2, rr = r & 3;
+        const int k3 = g + ((rr >= 2) ? 8 : 0), k4 = 8 * nt + 2 * t + (rr & 1);
+        double2* row = reinterpret_cast<double2*>(P + (int64_t)(16 * k4 + k3) * p.inner + kA0);
+        double2 v0 = row[0], v1 = row[1];
+        v0.x += kFoldB * (double)acc[0][r];
+        v0.y += kFoldB * (double)acc[1][r];
+        v1.x += kFoldB * (double)acc[2][r];
+        v1.y += kFoldB * (double)acc[3][r];
+        row[0] = v0;
+        row[1] = v1;
     }
 }
 
@@ -399,24 +409,23 @@ bool tc_supports(const int32_t* n, int D, int dtype_is_ci8) {
     return D == 4 && n[0] == 16 && n[1] == 16 && n[2] == 8 && n[3] == 8 && dtype_is_ci8;
 }
 
-// Dynamic shared memory reserved (unused) by each stage-B CTA so that only one
-// fits per SM, leaving registers for stage-A CTAs of the next chunk to run
-// beside it (OMNI_TCB_PER_SM=1); 0 keeps two stage-B CTAs per SM.
-size_t stage_b_pad() {
-    static const size_t pad = [] {
-        const char* env = std::getenv("OMNI_TCB_PER_SM");
-        return (env && std::atoi(env) == 1) ? (size_t)100 * 1024 : (size_t)0;
+int tc_stage_b_tile() { return kB2Warps * kB2KPW; }
+
+// Stage-B form: next-sample register prefetch with shared-memory GEMM 4
+// fragments (default), or OMNI_TCB_PREFETCH=0 for register fragments and
+// loads at the top of each sample.
+void (*stage_b_kernel())(Pass, PassArgs) {
+    static const bool prefetch = [] {
+        const char* env = std::getenv("OMNI_TCB_PREFETCH");
+        return !(env && std::atoi(env) == 0);
     }();
-    return pad;
+    return prefetch ? tc_stage_b<true> : tc_stage_b<false>;
 }
 
 cudaError_t tc_occupancy(int kind, int* blocks_per_sm) {
     if (kind == KIND_TC_A)
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, tc_stage_a, kStageAWarps * 32, 0);
-    cudaError_t e = smem_limit_once((const void*)tc_stage_b, stage_b_pad());
-    if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, tc_stage_b, kStageBWarps * 32,
-                                                         stage_b_pad());
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, stage_b_kernel(), kB2Warps * 32, 0);
 }
 
 cudaError_t launch_tc(const Pass& p, const PassArgs& a, cudaStream_t st) {
@@ -429,15 +438,10 @@ cudaError_t launch_tc(const Pass& p, const PassArgs& a, cudaStream_t st) {
         tc_stage_a<<<(unsigned)blocks, kStageAWarps * 32, 0, st>>>(p, a);
         return cudaGetLastError();
     }
-    if (a.src_kind != SRC_BUF || p.inner % kTileKA) return cudaErrorInvalidValue;
-    const int64_t blocks = a.S * (p.inner / kTileKA);
-    if (blocks <= 0) return cudaSuccess;
-    const size_t pad = stage_b_pad();
-    if (pad) {
-        cudaError_t e = smem_limit_once((const void*)tc_stage_b, pad);
-        if (e != cudaSuccess) return e;
-    }
-    tc_stage_b<<<(unsigned)blocks, kStageBWarps * 32, pad, st>>>(p, a);
+    if (a.src_kind != SRC_BUF || p.inner % kB2KPW) return cudaErrorInvalidValue;
+    const int64_t warps = a.S * (p.inner / kB2KPW);
+    if (warps <= 0) return cudaSuccess;
+    stage_b_kernel()<<<(unsigned)((warps + kB2Warps - 1) / kB2Warps), kB2Warps * 32, 0, st>>>(p, a);
     return cudaGetLastError();
 }
 
