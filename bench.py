@@ -199,7 +199,7 @@ def units_per_launch(stat, profiled_units):
     return profiled_units / max(1, stat["launches"])
 
 
-def roofline(stats, workload, path_precision, profiled_units=0):
+def roofline(stats, workload, path_precision, profiled_units=0, serial_shares=None):
     """Roofline of the dominant kernel (largest share of the event-timed region)."""
     timed = [s for s in stats if s["launches"] > 0 and s["total_ms"] > 0]
     if not timed:
@@ -237,6 +237,7 @@ def roofline(stats, workload, path_precision, profiled_units=0):
                  "kernel": top["name"], "flops_per_launch": flops_per_launch,
                  "avg_launch_ms": avg_s * 1e3,
                  "share_of_kernel_time": round(top["total_ms"] / total, 4),
+                 "share_serial": (serial_shares or {}).get(top["name"]),
                  "hbm": hbm})
     return main
 
@@ -417,6 +418,23 @@ def run_ours(args):
     head = results[args.precision]
     plan, vis = head["plan"], head["vis"]
 
+    # kernel shares without the two-stream chunk overlap (event spans of
+    # concurrent kernels overlap, so the headline run's shares are not serial
+    # shares; these are the ones an ncu launch list, serialised, can confirm)
+    serial = None
+    if rank == 0:
+        os.environ["OMNI_OVERLAP"] = "0"
+        try:
+            sp = omni.Plan(w.levels, w.channels, dtype=w.dtype, precision=args.precision)
+        finally:
+            del os.environ["OMNI_OVERLAP"]
+        svis = torch.empty_like(vis)
+        _, sstats = timed_steps(sp, x, svis, 2, 3, stream, lambda: None, True)
+        sp.close()
+        del svis
+        tot = sum(st["total_ms"] for st in sstats if st["launches"])
+        serial = {st["name"]: round(st["total_ms"] / tot, 4) for st in sstats if st["launches"]}
+
     # physical-baseline epilogue: radial profile of the step's visibilities
     epilogue = None
     if rank == 0:
@@ -443,17 +461,22 @@ def run_ours(args):
     if not args.no_e2e:
         xh = x.cpu().pin_memory()
         vh = torch.empty((w.channels, plan.n_lags), dtype=torch.complex128).pin_memory()
-        plan.correlate_host(xh)
-        plan.visibilities_host(reset=True, out=vh)
-        n_e2e = max(1, min(args.steps, 3))
-        barrier()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(n_e2e):
+        for _ in range(2):
             plan.correlate_host(xh)
             plan.visibilities_host(reset=True, out=vh)
-        torch.cuda.synchronize()
-        dt = (time.perf_counter() - t0) / n_e2e
+        # per-step wall times, median (single host-side outliers of 2-3x were
+        # seen on the first steps after a large pinned allocation)
+        n_e2e = max(3, min(args.steps, 5))
+        times = []
+        for _ in range(n_e2e):
+            barrier()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            plan.correlate_host(xh)
+            plan.visibilities_host(reset=True, out=vh)
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+        dt = statistics.median(times)
         e2e_rate, e2e_s = multirank.job_rate(units, dt, device=dev)
         e2e = {"value": e2e_rate, "unit": UNIT,
                "h2d_bytes_per_step": xh.numel() * xh.element_size(),
@@ -484,7 +507,7 @@ def run_ours(args):
                                parallelism=f"{world} ranks x {w.channels} channels"
                                if world > 1 else "single GPU"),
                 "roofline": roofline(stats, args.workload, args.precision,
-                                     w.channels * w.samples * args.steps),
+                                     w.channels * w.samples * args.steps, serial),
                 "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": sum(s["launches"] for s in stats),
                 "clocks": clocks, "epilogue": epilogue, "direct_n2": n2,
