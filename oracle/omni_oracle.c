@@ -258,6 +258,81 @@ void oracle_correlate_selected(int D, const int32_t *n, int64_t C, int64_t T, in
     }
 }
 
+/*
+ * Beam-space variant (Appendix A, steps 4 and 5), in those two steps:
+ *
+ *   4. every level-1 block (dimensions 0 and 1, sizes n1 x n2) is Fourier
+ *      transformed without padding, giving n1 x n2 digital pointings k:
+ *        y_t(k; m') = sum_{a < n1, b < n2} x_t(a, b, m')
+ *                     * exp(-2 pi i (k_a a / n1 + k_b b / n2)),
+ *      evaluated term by term (a direct DFT, no FFT);
+ *   5. each pointing is correlated over the remaining dimensions (levels
+ *      2..n) by the same brute-force definition as oracle_correlate:
+ *        B_c(k; D') = sum_t sum_{m'} y_t(k; m' + D') conj(y_t(k; m')).
+ *
+ * x is [C][T][N] of type dtype (antenna order dimension 0 fastest, so
+ * antenna a + n1 (b + n2 m')); B is [C][Q'][n1 n2][2] with Q' = prod_{d >= 2}
+ * (2 n_d - 1), lags in oracle_lag_table order over dimensions 2.., pointing
+ * index k_a + n1 k_b fastest.  Needs D >= 3.
+ */
+void oracle_beam_correlate(int D, const int32_t *n, int64_t C, int64_t T, int dtype,
+                           const void *x, double *B)
+{
+    const int32_t n1 = n[0], n2 = n[1];
+    const int64_t nb = (int64_t)n1 * n2;
+    const int Dc = D - 2;
+    const int32_t *nc = n + 2;
+    const int64_t Nc = oracle_n_antennas(Dc, nc);
+    const int64_t Qc = oracle_n_lags(Dc, nc);
+    const int64_t N = nb * Nc;
+    int64_t stride[OR_MAX_DIMS];
+    int64_t s = 1;
+    for (int d = 0; d < Dc; ++d) { stride[d] = s; s *= nc[d]; }
+    const double two_pi = 6.283185307179586476925286766559;
+    size_t eb = elem_bytes(dtype);
+    double *y = (double *)malloc(sizeof(double) * 2 * (size_t)(nb * T * Nc));
+    if (!y) return;
+    for (int64_t c = 0; c < C; ++c) {
+        const char *xc = (const char *)x + (size_t)(c * T * N) * eb;
+        /* step 4: y[k][t][m'] */
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int64_t k = 0; k < nb; ++k) {
+            const int64_t ka = k % n1, kb = k / n1;
+            for (int64_t t = 0; t < T; ++t) {
+                const char *xt = xc + (size_t)(t * N) * eb;
+                for (int64_t mc = 0; mc < Nc; ++mc) {
+                    double sre = 0.0, sim = 0.0;
+                    for (int64_t b = 0; b < n2; ++b)
+                        for (int64_t a = 0; a < n1; ++a) {
+                            double xr, xi;
+                            load_x(xt, dtype, a + n1 * (b + n2 * mc), &xr, &xi);
+                            const double ph = -two_pi * ((double)((ka * a) % n1) / n1 +
+                                                         (double)((kb * b) % n2) / n2);
+                            const double wr = cos(ph), wi = sin(ph);
+                            sre += xr * wr - xi * wi;
+                            sim += xr * wi + xi * wr;
+                        }
+                    double *o = y + 2 * ((k * T + t) * Nc + mc);
+                    o[0] = sre;
+                    o[1] = sim;
+                }
+            }
+        }
+        /* step 5: brute-force correlation of each pointing over levels 2..n */
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int64_t k = 0; k < nb; ++k) {
+            const double *yk = y + 2 * (k * T * Nc);
+            for (int64_t q = 0; q < Qc; ++q) {
+                int32_t lag[OR_MAX_DIMS];
+                lag_of_index(Dc, nc, q, lag);
+                double *o = B + 2 * ((c * Qc + q) * nb + k);
+                one_lag(Dc, nc, stride, Nc, T, yk, 0, lag, &o[0], &o[1]);
+            }
+        }
+    }
+    free(y);
+}
+
 int oracle_max_dims(void) { return OR_MAX_DIMS; }
 
 /* Threads the OpenMP loops above use. */

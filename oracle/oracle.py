@@ -6,7 +6,9 @@ bench.py's CPU-baseline leg, never by the product package.
 What the oracle computes is the plain brute-force definition of the summed
 visibilities (Eq. ConvolutionDefEq, Sec. II.C; Eq. ProofEq2, Sec. II.D):
 V_c(D) = sum_t sum_m x_{c,t}(m+D) conj(x_{c,t}(m)), plus the lag table with
-its redundancy counts (Sec. III) and the geometry of Eq. GridEq.
+its redundancy counts (Sec. III), the geometry of Eq. GridEq, and the
+beam-space variant of Appendix A (steps 4-5: direct DFT of each level-1
+block into pointings, brute-force correlation over the coarser levels).
 """
 from __future__ import annotations
 
@@ -65,6 +67,9 @@ def lib() -> ctypes.CDLL:
         L.oracle_correlate_selected.argtypes = [ctypes.c_int, i32p, ctypes.c_int64,
                                                 ctypes.c_int64, ctypes.c_int, ctypes.c_void_p,
                                                 ctypes.c_int64, i64p, i64p, f64p]
+        L.oracle_beam_correlate.restype = None
+        L.oracle_beam_correlate.argtypes = [ctypes.c_int, i32p, ctypes.c_int64, ctypes.c_int64,
+                                            ctypes.c_int, ctypes.c_void_p, f64p]
         L.oracle_max_dims.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -165,6 +170,26 @@ def correlate_selected(dims: Sequence[int], x, chans, lag_idx) -> np.ndarray:
                                     _ptr(ch, ctypes.c_int64), _ptr(lq, ctypes.c_int64),
                                     _ptr(V, ctypes.c_double))
     return V[:, 0] + 1j * V[:, 1]
+
+
+def beam_correlate(dims: Sequence[int], x) -> np.ndarray:
+    """Beam-space visibilities (Appendix A steps 4-5), complex128 [C][Q'][n1*n2]:
+    an unpadded direct DFT of every level-1 block (dims[0], dims[1]) into
+    pointings, then the brute-force correlation of each pointing over the
+    remaining dimensions (lags in lag_table(dims[2:]) order, pointing fastest)."""
+    d = _i32(dims)
+    if len(d) < 3:
+        raise ValueError("the beam-space variant needs a coarser level")
+    a, code = _as_input(x)
+    C, T, N = a.shape[0], a.shape[1], a.shape[2]
+    if N != int(np.prod(d)):
+        raise ValueError("voltage length does not match the lattice")
+    Qc = n_lags(d[2:])
+    nb = int(d[0]) * int(d[1])
+    B = np.zeros((C, Qc, nb, 2))
+    lib().oracle_beam_correlate(len(d), _ptr(d, ctypes.c_int32), C, T, code,
+                                a.ctypes.data_as(ctypes.c_void_p), _ptr(B, ctypes.c_double))
+    return B[..., 0] + 1j * B[..., 1]
 
 
 # ---------------------------------------------------------------- physical baselines

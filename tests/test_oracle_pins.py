@@ -320,3 +320,77 @@ def test_group_sum_of_correlation_equals_pairs_by_physical_separation():
                 g = int(np.argmin(np.hypot(*(reps - (r[i] - r[j])).T)))
                 expect[g] += xc[0, t, i] * np.conj(xc[0, t, j])
     np.testing.assert_allclose(merged[0], expect, rtol=0, atol=1e-10)
+
+
+# ---------------------------------------------------------------- beam-space variant
+
+BEAM_LAYOUTS = [
+    [synth.Level(4, 2), synth.Level(3, 2, (5.0, 0.0, 0.0, 5.0))],
+    [synth.Level(3, 3), synth.Level(2, 2, (4.0, 0.5, 0.0, 4.0)), synth.Level(2, 1, (10.0, 0.0, 0.0, 10.0))],
+    [synth.Level(5, 1), synth.Level(1, 4, (7.0, 0.0, 0.0, 7.0))],
+]
+
+
+@pytest.mark.parametrize("levels", BEAM_LAYOUTS)
+def test_beam_sum_is_the_zero_level1_lag_slice(levels):
+    """Summed over pointings, |DFT|^2 is Parseval's n1 n2 sum over the block,
+    so sum_k B(k; D') = n1 n2 V(0, 0, D') of the full 2n-D correlator."""
+    dims = synth.lattice_dims(levels)
+    x = synth.random_complex(dims, 2, 3, seed=41)
+    B = oracle.beam_correlate(dims, x)
+    V = oracle.correlate(dims, x)
+    lags = _lag_vectors(dims)
+    sel = np.where((lags[:, 0] == 0) & (lags[:, 1] == 0))[0]
+    assert relerr(B.sum(axis=2), dims[0] * dims[1] * V[:, sel]) < 1e-12
+
+
+@pytest.mark.parametrize("levels", BEAM_LAYOUTS)
+def test_beam_all_ones(levels):
+    """All-ones blocks put n1 n2 in pointing 0 only: B(0; D') = (n1 n2)^2 T prod (n_d - |D_d|)."""
+    dims = synth.lattice_dims(levels)
+    T = 2
+    B = oracle.beam_correlate(dims, synth.all_ones(dims, 1, T))
+    lags = _lag_vectors(dims[2:])
+    red = np.prod([n - np.abs(lags[:, d]) for d, n in enumerate(dims[2:])], axis=0)
+    nb = dims[0] * dims[1]
+    np.testing.assert_allclose(B[0, :, 0].real, nb * nb * T * red, rtol=1e-12, atol=1e-9)
+    assert np.abs(B[0, :, 0].imag).max() < 1e-9
+    assert np.abs(B[0, :, 1:]).max() < 1e-9
+
+
+def test_beam_separable_plane_wave():
+    """x(a, b, m') = exp(2 pi i (ka a / n1 + kb b / n2)) g(m') lands in pointing
+    (ka, kb) alone, with B = (n1 n2)^2 times the coarse lattice's own correlation of g."""
+    levels = BEAM_LAYOUTS[0]
+    dims = synth.lattice_dims(levels)
+    n1, n2, cdims = dims[0], dims[1], dims[2:]
+    ka, kb = 3, 1
+    rng = np.random.default_rng(5)
+    T, Nc = 3, int(np.prod(cdims))
+    g = rng.standard_normal((1, T, Nc)) + 1j * rng.standard_normal((1, T, Nc))
+    a = np.arange(n1)[None, :]
+    b = np.arange(n2)[:, None]
+    w = np.exp(2j * math.pi * (ka * a / n1 + kb * b / n2)).ravel()       # [n2 * n1], a fastest
+    x = (g[:, :, :, None] * w[None, None, None, :]).reshape(1, T, Nc * n1 * n2)
+    B = oracle.beam_correlate(dims, x)
+    Vg = oracle.correlate(cdims, g)
+    k = ka + n1 * kb
+    assert relerr(B[:, :, k], (n1 * n2) ** 2 * Vg) < 1e-12
+    others = np.delete(B, k, axis=2)
+    assert np.abs(others).max() < 1e-9 * np.abs(B[:, :, k]).max()
+
+
+def test_beam_numpy_route():
+    """numpy: unpadded fft2 over each block, then the zero-padded FFT route of
+    Sec. II.C over the remaining axes, per pointing."""
+    levels = BEAM_LAYOUTS[1]
+    dims = synth.lattice_dims(levels)
+    x = _cplx(synth.random_complex(dims, 1, 2, seed=43).numpy())
+    C, T, N = x.shape
+    n1, n2, cdims = dims[0], dims[1], dims[2:]
+    Nc = int(np.prod(cdims))
+    blocks = x.reshape(C, T, Nc, n2, n1)
+    y = np.fft.fft2(blocks, axes=(3, 4))                                  # [C][T][Nc][kb][ka]
+    y = y.reshape(C, T, Nc, n1 * n2).transpose(0, 3, 1, 2)                 # [C][k][T][Nc]
+    ref = np.stack([fft_route(cdims, y[:, k]) for k in range(n1 * n2)], axis=2)
+    assert relerr(oracle.beam_correlate(dims, x), ref) < 1e-12
