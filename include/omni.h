@@ -101,6 +101,22 @@ omni_status omni_baselines(const omni_level* levels, int n_levels, int32_t* dm,
 omni_status omni_plan_create(const omni_level* levels, int n_levels, int64_t n_channels,
                              omni_dtype dtype, omni_precision precision, omni_plan** out);
 
+/* Beam-space plan (Appendix A, steps 4-5): each level-1 block is Fourier
+ * transformed unpadded, giving n1 x n2 digital pointings k = (k_a, k_b), and
+ * the correlation runs over the axes of levels 2..n only:
+ *   y_t(k; m') = sum_{m1} x_t(m1, m') exp(-2 pi i (k_a m1_a / n1 + k_b m1_b / n2)),
+ *   B_c(k; D') = sum_t sum_{m'} y_t(k; m' + D') conj(y_t(k; m')),
+ * with m' the index on levels 2..n and D' its lag.  omni_correlate* take the
+ * same voltages [C][T][N]; omni_visibilities* write B as complex128
+ * [C][Q'][n1 n2], the pointing index k_a + n1 k_b fastest and the lags of
+ * levels 2..n in the order omni_baselines gives for levels + 1 (the lag table
+ * of the coarser levels alone).  omni_plan_info reports n_lags = Q' n1 n2 and
+ * the level-1 axes as unpadded.  FP32 path only.
+ * Errors: as omni_plan_create; UNSUPPORTED for a single level or when every
+ * coarser level is 1 x 1. */
+omni_status omni_plan_create_beams(const omni_level* levels, int n_levels, int64_t n_channels,
+                                   omni_dtype dtype, omni_plan** out);
+
 /* A plan for n_arrays independent arrays of possibly different hierarchies
  * (Sec. III: several separate omniscopes, each correlated on its own), all with
  * n_channels channels of the same dtype.  levels_per_array[a] has

@@ -49,6 +49,9 @@ omni_status cuda_fail(cudaError_t e, const char* what) {
 
 bool is_pow2(int64_t x) { return x > 0 && (x & (x - 1)) == 0; }
 
+struct Geometry;
+double inverse_length(const Geometry& g, bool beams);
+
 // Lattice geometry of a validated hierarchy.
 struct Geometry {
     int n_levels = 0;
@@ -59,7 +62,9 @@ struct Geometry {
     std::vector<double> A;  // [n_levels][4]
 };
 
-omni_status make_geometry(const omni_level* levels, int n_levels, Geometry& g) {
+// beams: the level-1 axes are transformed unpadded (n_d points -> n_d digital
+// pointings, Appendix A step 4); they carry the pointing index, not a lag.
+omni_status make_geometry(const omni_level* levels, int n_levels, Geometry& g, bool beams = false) {
     if (!levels) return fail(OMNI_ERR_INVALID_ARG, "levels is NULL");
     if (n_levels < 1 || n_levels > kMaxDims / 2)
         return fail(OMNI_ERR_INVALID_ARG, "n_levels must be in [1, %d], got %d", kMaxDims / 2, n_levels);
@@ -80,17 +85,26 @@ omni_status make_geometry(const omni_level* levels, int n_levels, Geometry& g) {
     }
     for (int d = 0; d < g.D; ++d) {
         const int64_t nd = g.n[d];
-        const int64_t Ld = nd > 1 ? 2 * nd : 1;
+        const bool beam_axis = beams && d < 2;
+        const int64_t Ld = (nd > 1 && !beam_axis) ? 2 * nd : nd;
         if (g.N > (int64_t(1) << 40) / nd) return fail(OMNI_ERR_UNSUPPORTED, "too many antennas");
         g.N *= nd;
         g.L *= Ld;
-        g.Q *= 2 * nd - 1;
+        g.Q *= beam_axis ? nd : 2 * nd - 1;
         if (Ld > kTwiddleN) return fail(OMNI_ERR_UNSUPPORTED, "padded axis %d has length %lld > %d", d, (long long)Ld, kTwiddleN);
         if (!is_pow2(Ld) && Ld > 1024)
             return fail(OMNI_ERR_UNSUPPORTED, "padded axis %d has non-power-of-two length %lld > 1024", d, (long long)Ld);
         g.Lp[d] = (int32_t)Ld;
     }
     return OMNI_OK;
+}
+
+// Points of the inverse transform (the 1/L of Eq. ProofEq2's inverse FFT):
+// every padded axis, or for a beam-space plan the axes of levels 2..n.
+double inverse_length(const Geometry& g, bool beams) {
+    double L = 1.0;
+    for (int d = beams ? 2 : 0; d < g.D; ++d) L *= (double)g.Lp[d];
+    return L;
 }
 
 // Antenna positions r_i = sum_k A_k m_k (Eq. GridEq), antenna order dimension 0 fastest.
@@ -169,6 +183,7 @@ struct omni_plan {
     std::vector<Pass> fwd, inv;
     int64_t Cc = 1, Tc = 1;   // forward chunk: channels x samples
     int64_t chunk_mb = 1536;  // target size of each chunk scratch buffer
+    bool beams = false;       // beam-space plan: level-1 axes unpadded, no lag over them
     int64_t Cv = 1;           // inverse batch: channels
     int64_t fwd_elems = 0;    // float2 per sample, largest non-final forward output
     int64_t inv_elems = 0;    // float2 per channel, largest non-final inverse output
@@ -236,7 +251,7 @@ int elem_bytes(omni_dtype t) { return t == OMNI_IN_CI8 ? 2 : 8; }
 void choose_kind(Pass& p) {
     if (p.L == 1) {
         p.kind = KIND_DIRECT;
-    } else if (is_pow2(p.L) && p.L <= 64) {
+    } else if (is_pow2(p.L) && p.L >= 4 && p.L <= 64) {
         p.kind = KIND_REG;
     } else if (is_pow2(p.L) && p.L <= kTwiddleN) {
         p.kind = KIND_SMEM;
@@ -282,7 +297,8 @@ omni_status build_passes(omni_plan* pl) {
     for (size_t a = 0; a < axes.size(); ++a) {
         const int d = axes[a];
         const bool pair = use_level && (d % 2 == 0) && a + 1 < axes.size() && axes[a + 1] == d + 1 &&
-                          g.Lp[d] == g.Lp[d + 1] && is_pow2(g.Lp[d]) && g.Lp[d] <= 64;
+                          g.Lp[d] == g.Lp[d + 1] && is_pow2(g.Lp[d]) && g.Lp[d] <= 64 &&
+                          !(pl->beams && d < 2);
         stages.push_back({d, pair});
         if (pair) ++a;
     }
@@ -336,6 +352,9 @@ omni_status build_passes(omni_plan* pl) {
             choose_level(p);
         } else {
             choose_kind(p);
+            // unpadded (beam) axes: full-length register FFTs up to 64 points,
+            // direct DFTs otherwise (the shared-memory kernels assume padding)
+            if (p.n == p.L && p.L > 1 && p.kind == KIND_SMEM) p.kind = KIND_DIRECT;
         }
         if (p.mode == MODE_MID) pl->fwd_elems = std::max(pl->fwd_elems, p.outer * p.q_out * p.inner);
         pl->fwd.push_back(p);
@@ -343,8 +362,13 @@ omni_status build_passes(omni_plan* pl) {
     // inverse: decreasing axis order; inputs [outer Q_e>d][L_d][inner L_e<d]
     pl->inv.clear();
     pl->inv_elems = 0;
-    for (size_t a = axes.size(); a-- > 0;) {
-        const int d = axes[a];
+    std::vector<int> inv_axes;
+    for (int d : axes)
+        if (!(pl->beams && d < 2)) inv_axes.push_back(d);
+    if (inv_axes.empty())
+        return fail(OMNI_ERR_UNSUPPORTED, "a beam-space plan needs a coarser level with more than one block");
+    for (size_t a = inv_axes.size(); a-- > 0;) {
+        const int d = inv_axes[a];
         Pass p{};
         p.axis = d;
         p.L = g.Lp[d];
@@ -380,8 +404,8 @@ omni_status build_passes(omni_plan* pl) {
 }
 
 // Chunk sizes: the last pass gets one wave of resident CTAs (channels x inner
-// tiles), and each scratch buffer holds about chunk_mb MB of samples (1536 for
-// a single array, 256 for each member of a batch; OMNI_CHUNK_MB overrides):
+// tiles), and each scratch buffer holds about chunk_mb MB of samples (1536;
+// OMNI_CHUNK_MB overrides):
 // long chunks amortise the FP64 fold and the launch ramp (measured on the
 // 2-level workload, FP32 path: 96 MB 33.7 ms, 192 MB 26.6, 384 MB 22.6,
 // 768 MB 21.3, 1536 MB 20.8 ms per step).
@@ -675,7 +699,7 @@ omni_status run_inverse(omni_plan* pl, double2* V, cudaStream_t st) {
             if (p.mode == MODE_INV_LAST) {
                 a.V = V;
                 a.V_stride = pl->g.Q;
-                a.scale = 1.0 / (double)pl->g.L;
+                a.scale = 1.0 / inverse_length(pl->g, pl->beams);
             } else {
                 a.dst = dst;
                 a.dst_stride = p.outer * p.q_out * p.inner;
@@ -827,24 +851,34 @@ omni_status omni_unique_baselines(const omni_level* levels, int n_levels, int64_
 
 static omni_status create_plan(const omni_level* levels, int n_levels, int64_t n_channels,
                                omni_dtype dtype, omni_precision precision, int64_t chunk_mb,
-                               omni_plan** out);
+                               omni_plan** out, bool beams = false);
 
 omni_status omni_plan_create(const omni_level* levels, int n_levels, int64_t n_channels,
                              omni_dtype dtype, omni_precision precision, omni_plan** out) {
     return create_plan(levels, n_levels, n_channels, dtype, precision, 1536, out);
 }
 
+omni_status omni_plan_create_beams(const omni_level* levels, int n_levels, int64_t n_channels,
+                                   omni_dtype dtype, omni_plan** out) {
+    return create_plan(levels, n_levels, n_channels, dtype, OMNI_FP32, 1536, out, true);
+}
+
 static omni_status create_plan(const omni_level* levels, int n_levels, int64_t n_channels,
                                omni_dtype dtype, omni_precision precision, int64_t chunk_mb,
-                               omni_plan** out) {
+                               omni_plan** out, bool beams) {
     if (!out) return fail(OMNI_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (n_channels < 1) return fail(OMNI_ERR_INVALID_ARG, "n_channels must be >= 1");
     if (dtype != OMNI_IN_CF32 && dtype != OMNI_IN_CI8) return fail(OMNI_ERR_INVALID_ARG, "unknown dtype %d", (int)dtype);
     if (precision != OMNI_FP32 && precision != OMNI_MIXED_FP16)
         return fail(OMNI_ERR_INVALID_ARG, "unknown precision %d", (int)precision);
+    if (beams && precision != OMNI_FP32)
+        return fail(OMNI_ERR_UNSUPPORTED, "beam-space plans run the FP32 path");
+    if (beams && levels && n_levels < 2)
+        return fail(OMNI_ERR_UNSUPPORTED, "a beam-space plan needs at least two levels");
     omni_plan* pl = new omni_plan();
-    omni_status st = make_geometry(levels, n_levels, pl->g);
+    pl->beams = beams;
+    omni_status st = make_geometry(levels, n_levels, pl->g, beams);
     if (st == OMNI_OK) st = check_unique(pl->g);
     if (st != OMNI_OK) {
         delete pl;
@@ -994,7 +1028,7 @@ omni_status omni_plan_create_batch(const omni_level* const* levels_per_array,
         while (b < n_arrays && same_shape(a, b)) ++b;
         omni_plan* sub = nullptr;
         omni_status st = create_plan(levels_per_array[a], n_levels_per_array[a],
-                                     (int64_t)(b - a) * n_channels, dtype, precision, 256, &sub);
+                                     (int64_t)(b - a) * n_channels, dtype, precision, 1536, &sub);
         if (st != OMNI_OK) {
             release(pl);
             return st;

@@ -4,7 +4,8 @@
 // Register passes: one thread per line, the whole (power-of-two, <= 64) line
 // held in registers.  A forward pass reads the n_d measured values of a line
 // and produces all L_d = 2 n_d frequencies (zero padding never stored; the
-// first radix-2 stage is twiddles only).  The last forward pass squares the
+// first radix-2 stage is twiddles only; a beam-space pointing axis, n_d = L_d,
+// is transformed whole).  The last forward pass squares the
 // modulus and sums over the chunk's samples before folding into FP64.  An
 // inverse pass transforms a full line and keeps the 2 n_d - 1 lag bins.
 #include "omni_fft_common.cuh"
@@ -53,13 +54,17 @@ __global__ void __launch_bounds__(256) pass_reg(Pass p, PassArgs a) {
         const int64_t r = flat - s * lines;
         const int64_t o = r / inner, i = r - o * inner;
         const int64_t base = src_base(a, s) + o * p.n * inner + i;
+        // an unpadded forward line (n == L: a beam-space pointing axis) is a full
+        // transform; otherwise the upper half is the zero padding
+        const bool full = !FWD || p.n == L;
         float2 v[L];
 #pragma unroll
         for (int j = 0; j < L; ++j) {
-            const bool live = FWD ? (j < L / 2) : true;
+            const bool live = full || j < L / 2;
             v[j] = live ? ld_src<SRC>(src, base + (int64_t)j * inner) : make_float2(0.f, 0.f);
         }
-        fft_dif<L, FWD>(v);
+        if (full) fft_dif<L, false>(v);
+        else fft_dif<L, true>(v);
         if constexpr (MODE == MODE_MID) {
             float2* d = a.dst + s * a.dst_stride + o * (int64_t)L * inner + i;
 #pragma unroll

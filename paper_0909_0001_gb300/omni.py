@@ -33,7 +33,7 @@ EXPORTS = (
     "omni_visibilities_host", "omni_reset", "omni_sync", "omni_last_error",
     "omni_status_string", "omni_profile_enable", "omni_profile_read", "omni_correlate_noalloc",
     "omni_plan_create_batch", "omni_batch_info", "omni_radial_bins", "omni_unique_baselines",
-    "omni_sum_groups",
+    "omni_sum_groups", "omni_plan_create_beams",
 )
 
 
@@ -72,6 +72,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "omni_baselines": (ctypes.c_int, [lv, ctypes.c_int, P(i32), P(i64), P(dbl)]),
         "omni_plan_create": (ctypes.c_int, [lv, ctypes.c_int, i64, ctypes.c_int, ctypes.c_int,
                                             P(vp)]),
+        "omni_plan_create_beams": (ctypes.c_int, [lv, ctypes.c_int, i64, ctypes.c_int, P(vp)]),
         "omni_plan_destroy": (None, [vp]),
         "omni_plan_info": (ctypes.c_int, [vp, P(ctypes.c_int), P(i32), P(i32), P(i64), P(i64),
                                           P(i64)]),
@@ -211,9 +212,7 @@ class Plan:
         self.channels = int(channels)
         self.dtype = dtype
         self.precision = precision
-        h = ctypes.c_void_p()
-        _check(load().omni_plan_create(_levels(levels), len(levels), self.channels,
-                                       DTYPES[dtype], PRECISIONS[precision], ctypes.byref(h)))
+        h = self._create()
         self._h = h
         nd = ctypes.c_int()
         dims = (ctypes.c_int32 * 16)()
@@ -225,6 +224,13 @@ class Plan:
         self.padded = [pad[d] for d in range(nd.value)]
         self.n_antennas = N.value
         self.n_lags = Q.value
+
+    def _create(self) -> ctypes.c_void_p:
+        h = ctypes.c_void_p()
+        _check(load().omni_plan_create(_levels(self.levels), len(self.levels), self.channels,
+                                       DTYPES[self.dtype], PRECISIONS[self.precision],
+                                       ctypes.byref(h)))
+        return h
 
     # ---------------------------------------------------------------- checks
     def _check_volts(self, v: torch.Tensor) -> int:
@@ -318,6 +324,29 @@ class Plan:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class BeamPlan(Plan):
+    """Beam-space correlator (Appendix A, steps 4-5): every level-1 block is
+    Fourier transformed unpadded into n1 x n2 digital pointings, and each
+    pointing is correlated over the axes of levels 2..n.  visibilities()
+    returns [C][Q' * n1 * n2] complex128, the pointing index fastest; split()
+    views it as [C][Q'][k_b][k_a], with the Q' lags of baselines(levels[1:])."""
+
+    def __init__(self, levels: Sequence[Level], channels: int, dtype: str = "cf32"):
+        super().__init__(levels, channels, dtype=dtype, precision="fp32")
+        self.beam_shape = (int(self.levels[0].n1), int(self.levels[0].n2))
+        self.n_beams = self.beam_shape[0] * self.beam_shape[1]
+        self.n_coarse_lags = self.n_lags // self.n_beams
+
+    def _create(self) -> ctypes.c_void_p:
+        h = ctypes.c_void_p()
+        _check(load().omni_plan_create_beams(_levels(self.levels), len(self.levels),
+                                             self.channels, DTYPES[self.dtype], ctypes.byref(h)))
+        return h
+
+    def split(self, V: torch.Tensor) -> torch.Tensor:
+        return V.reshape(self.channels, self.n_coarse_lags, self.beam_shape[1], self.beam_shape[0])
 
 
 class BatchPlan(Plan):
