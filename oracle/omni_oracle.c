@@ -333,6 +333,54 @@ void oracle_beam_correlate(int D, const int32_t *n, int64_t C, int64_t T, int dt
     free(y);
 }
 
+/*
+ * Tile hybrid (the variant of Sec. III that FFT-correlates within tiles and
+ * correlates the tiles' beams pairwise): n_tiles identical n1 x n2 tiles at
+ * arbitrary offsets.  For every ordered tile pair (i, j) and intra-tile lag
+ * D (D_d in [-(n_d-1), n_d-1]):
+ *
+ *   V_c(i, j; D) = sum_t sum_{m, m+D in the tile} x_{c,t,i}(m + D) conj(x_{c,t,j}(m)),
+ *
+ * the brute-force sum over the antenna pairs (a in tile i, b in tile j)
+ * with m_a - m_b = D.  x is [C][T][n_tiles * n1 * n2] (tile slowest, then
+ * dimension 1, dimension 0 fastest); V is [C][n_tiles][n_tiles][Q][2] with
+ * Q = (2 n1 - 1)(2 n2 - 1), lags dimension 0 fastest.
+ */
+void oracle_tile_correlate(int n1, int n2, int n_tiles, int64_t C, int64_t T, int dtype,
+                           const void *x, double *V)
+{
+    const int64_t M = (int64_t)n1 * n2, N = M * n_tiles;
+    const int64_t Q1 = 2 * (int64_t)n1 - 1, Q2 = 2 * (int64_t)n2 - 1, Q = Q1 * Q2;
+    size_t eb = elem_bytes(dtype);
+    for (int64_t c = 0; c < C; ++c) {
+        const char *xc = (const char *)x + (size_t)(c * T * N) * eb;
+#pragma omp parallel for collapse(2) schedule(dynamic, 1)
+        for (int64_t i = 0; i < n_tiles; ++i)
+            for (int64_t j = 0; j < n_tiles; ++j)
+                for (int64_t q = 0; q < Q; ++q) {
+                    const int64_t d1 = q % Q1 - (n1 - 1), d2 = q / Q1 - (n2 - 1);
+                    double sre = 0.0, sim = 0.0;
+                    for (int64_t t = 0; t < T; ++t) {
+                        const char *xt = xc + (size_t)(t * N) * eb;
+                        for (int64_t b = 0; b < n2; ++b) {
+                            if (b + d2 < 0 || b + d2 >= n2) continue;
+                            for (int64_t a = 0; a < n1; ++a) {
+                                if (a + d1 < 0 || a + d1 >= n1) continue;
+                                double ar, ai, br, bi;
+                                load_x(xt, dtype, i * M + (a + d1) + n1 * (b + d2), &ar, &ai);
+                                load_x(xt, dtype, j * M + a + n1 * b, &br, &bi);
+                                sre += ar * br + ai * bi;
+                                sim += ai * br - ar * bi;
+                            }
+                        }
+                    }
+                    double *o = V + 2 * (((c * n_tiles + i) * n_tiles + j) * Q + q);
+                    o[0] = sre;
+                    o[1] = sim;
+                }
+    }
+}
+
 int oracle_max_dims(void) { return OR_MAX_DIMS; }
 
 /* Threads the OpenMP loops above use. */

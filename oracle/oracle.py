@@ -8,7 +8,9 @@ visibilities (Eq. ConvolutionDefEq, Sec. II.C; Eq. ProofEq2, Sec. II.D):
 V_c(D) = sum_t sum_m x_{c,t}(m+D) conj(x_{c,t}(m)), plus the lag table with
 its redundancy counts (Sec. III), the geometry of Eq. GridEq, and the
 beam-space variant of Appendix A (steps 4-5: direct DFT of each level-1
-block into pointings, brute-force correlation over the coarser levels).
+block into pointings, brute-force correlation over the coarser levels) and the
+tile hybrid of Sec. III (brute-force correlation of every ordered tile pair at
+every intra-tile offset).
 """
 from __future__ import annotations
 
@@ -70,6 +72,9 @@ def lib() -> ctypes.CDLL:
         L.oracle_beam_correlate.restype = None
         L.oracle_beam_correlate.argtypes = [ctypes.c_int, i32p, ctypes.c_int64, ctypes.c_int64,
                                             ctypes.c_int, ctypes.c_void_p, f64p]
+        L.oracle_tile_correlate.restype = None
+        L.oracle_tile_correlate.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int64,
+                                            ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, f64p]
         L.oracle_max_dims.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -190,6 +195,21 @@ def beam_correlate(dims: Sequence[int], x) -> np.ndarray:
     lib().oracle_beam_correlate(len(d), _ptr(d, ctypes.c_int32), C, T, code,
                                 a.ctypes.data_as(ctypes.c_void_p), _ptr(B, ctypes.c_double))
     return B[..., 0] + 1j * B[..., 1]
+
+
+def tile_correlate(n1: int, n2: int, n_tiles: int, x) -> np.ndarray:
+    """Tile-hybrid visibilities, complex128 [C][n_tiles][n_tiles][Q]: for each
+    ordered tile pair (i, j) the brute-force sum of x_i(m + D) conj(x_j(m)) over
+    the pairs of antennas with intra-tile offset D (lags dimension 0 fastest)."""
+    a, code = _as_input(x)
+    C, T, N = a.shape[0], a.shape[1], a.shape[2]
+    if N != n1 * n2 * n_tiles:
+        raise ValueError("voltage length does not match the tiles")
+    Q = (2 * n1 - 1) * (2 * n2 - 1)
+    V = np.zeros((C, n_tiles, n_tiles, Q, 2))
+    lib().oracle_tile_correlate(n1, n2, n_tiles, C, T, code, a.ctypes.data_as(ctypes.c_void_p),
+                                _ptr(V, ctypes.c_double))
+    return V[..., 0] + 1j * V[..., 1]
 
 
 # ---------------------------------------------------------------- physical baselines

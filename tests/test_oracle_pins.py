@@ -394,3 +394,64 @@ def test_beam_numpy_route():
     y = y.reshape(C, T, Nc, n1 * n2).transpose(0, 3, 1, 2)                 # [C][k][T][Nc]
     ref = np.stack([fft_route(cdims, y[:, k]) for k in range(n1 * n2)], axis=2)
     assert relerr(oracle.beam_correlate(dims, x), ref) < 1e-12
+
+
+# ---------------------------------------------------------------- tile hybrid
+
+def test_tile_diagonal_is_each_tile_alone():
+    n1, n2, nt = 3, 2, 4
+    x = synth.random_complex([n1, n2, nt], 2, 3, seed=51)
+    V = oracle.tile_correlate(n1, n2, nt, x)
+    for i in range(nt):
+        Vi = oracle.correlate([n1, n2], x[:, :, i * n1 * n2:(i + 1) * n1 * n2])
+        assert relerr(V[:, i, i], Vi) < 1e-14
+
+
+def test_tiles_on_a_lattice_reduce_to_the_two_level_hypercube():
+    """Tiles placed on a grid form a 2-level hierarchy; summing V_ij over the
+    tile pairs with the same tile-grid offset gives the hypercube's visibility
+    at (intra-tile lag, tile-grid lag)."""
+    n1, n2, N1, N2 = 3, 2, 3, 2
+    nt = N1 * N2
+    x = synth.random_complex([n1, n2, N1, N2], 1, 2, seed=52)
+    V = oracle.tile_correlate(n1, n2, nt, x)
+    H = oracle.correlate([n1, n2, N1, N2], x)
+    Q1, Q2 = 2 * n1 - 1, 2 * n2 - 1
+    R1, R2 = 2 * N1 - 1, 2 * N2 - 1
+    acc = np.zeros((Q1 * Q2, R1 * R2), dtype=complex)
+    for i in range(nt):
+        for j in range(nt):
+            D1 = (i % N1) - (j % N1) + (N1 - 1)
+            D2 = (i // N1) - (j // N1) + (N2 - 1)
+            acc[:, D1 + R1 * D2] += V[0, i, j]
+    # hypercube lag index: intra-tile lag fastest, then the tile-grid lag
+    assert relerr(acc.T.ravel(), H[0]) < 1e-13
+
+
+def test_tile_hermitian_and_all_ones():
+    n1, n2, nt = 4, 3, 3
+    x = synth.random_complex([n1, n2, nt], 1, 2, seed=53)
+    V = oracle.tile_correlate(n1, n2, nt, x)
+    Q = (2 * n1 - 1) * (2 * n2 - 1)
+    for i in range(nt):
+        for j in range(nt):
+            np.testing.assert_allclose(V[0, j, i][::-1], np.conj(V[0, i, j]), rtol=0, atol=1e-12)
+    T = 3
+    W = oracle.tile_correlate(n1, n2, nt, synth.all_ones([n1, n2, nt], 1, T))
+    lags = _lag_vectors([n1, n2])
+    red = (n1 - np.abs(lags[:, 0])) * (n2 - np.abs(lags[:, 1]))
+    assert W.shape == (1, nt, nt, Q)
+    np.testing.assert_array_equal(W[0].real, np.broadcast_to(T * red, (nt, nt, Q)))
+
+
+def test_tile_numpy_cross_spectrum_route():
+    """numpy: zero-padded fft2 of every tile, cross-spectra summed over time,
+    inverse fft2, gather the intra-tile lags."""
+    n1, n2, nt = 4, 3, 3
+    x = _cplx(synth.random_complex([n1, n2, nt], 1, 3, seed=54).numpy())
+    Y = np.fft.fft2(x.reshape(1, 3, nt, n2, n1), s=(2 * n2, 2 * n1), axes=(3, 4))
+    S = np.einsum("ctiab,ctjab->cijab", Y, np.conj(Y))
+    g = np.fft.ifft2(S, axes=(3, 4))
+    idx = np.ix_(np.arange(-(n2 - 1), n2) % (2 * n2), np.arange(-(n1 - 1), n1) % (2 * n1))
+    ref = g[..., idx[0], idx[1]].reshape(1, nt, nt, -1)
+    assert relerr(oracle.tile_correlate(n1, n2, nt, x), ref) < 1e-12
