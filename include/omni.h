@@ -117,6 +117,24 @@ omni_status omni_plan_create(const omni_level* levels, int n_levels, int64_t n_c
 omni_status omni_plan_create_beams(const omni_level* levels, int n_levels, int64_t n_channels,
                                    omni_dtype dtype, omni_plan** out);
 
+/* Tile hybrid (Sec. III): n_tiles identical tiles, each the one-level grid
+ * *tile (n1 x n2, matrix A), placed at arbitrary offsets o_j (offsets
+ * [n_tiles][2], metres, antenna j*n1*n2 + a + n1 b at o_j + A (a, b)).  Each
+ * tile is FFT-correlated within itself (zero-padded 2-D FFT per sample) and
+ * the tiles' spectra are correlated pairwise by brute force:
+ *   V_c(i, j; D) = sum_t sum_{m} x_{t,i}(m + D) conj(x_{t,j}(m)),
+ * for every ordered tile pair (i, j) and intra-tile offset D (the physical
+ * baseline is o_i - o_j + A D).  omni_correlate* take voltages [C][T][N]
+ * with N = n_tiles n1 n2, tile slowest; omni_visibilities* write complex128
+ * [C][n_tiles][n_tiles][(2 n1 - 1)(2 n2 - 1)], lags dimension 0 fastest.
+ * omni_plan_info reports dims (n1, n2, n_tiles, 1) and n_lags = n_tiles^2 Q.
+ * The plan's accumulator is [C][n_tiles][n_tiles][4 n1 n2] complex FP64.
+ * FP32 path only.  Errors: as omni_plan_create; INVALID_ARG for n_tiles < 1 or
+ * a NULL or non-finite offset; UNSUPPORTED beyond 4096 tiles; COLLISION if
+ * two antennas of different tiles coincide. */
+omni_status omni_plan_create_tiles(const omni_level* tile, int64_t n_tiles, const double* offsets,
+                                   int64_t n_channels, omni_dtype dtype, omni_plan** out);
+
 /* A plan for n_arrays independent arrays of possibly different hierarchies
  * (Sec. III: several separate omniscopes, each correlated on its own), all with
  * n_channels channels of the same dtype.  levels_per_array[a] has

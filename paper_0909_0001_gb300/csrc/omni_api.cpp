@@ -49,8 +49,10 @@ omni_status cuda_fail(cudaError_t e, const char* what) {
 
 bool is_pow2(int64_t x) { return x > 0 && (x & (x - 1)) == 0; }
 
+
 struct Geometry;
-double inverse_length(const Geometry& g, bool beams);
+omni_status tile_geometry(Geometry& g, int64_t n_tiles, const double* offsets);
+omni_status check_unique_positions(const std::vector<double>& r, int64_t N);
 
 // Lattice geometry of a validated hierarchy.
 struct Geometry {
@@ -99,14 +101,6 @@ omni_status make_geometry(const omni_level* levels, int n_levels, Geometry& g, b
     return OMNI_OK;
 }
 
-// Points of the inverse transform (the 1/L of Eq. ProofEq2's inverse FFT):
-// every padded axis, or for a beam-space plan the axes of levels 2..n.
-double inverse_length(const Geometry& g, bool beams) {
-    double L = 1.0;
-    for (int d = beams ? 2 : 0; d < g.D; ++d) L *= (double)g.Lp[d];
-    return L;
-}
-
 // Antenna positions r_i = sum_k A_k m_k (Eq. GridEq), antenna order dimension 0 fastest.
 void positions(const Geometry& g, std::vector<double>& r) {
     r.assign(2 * g.N, 0.0);
@@ -127,6 +121,36 @@ void positions(const Geometry& g, std::vector<double>& r) {
     }
 }
 
+// Tile hybrid: n_tiles copies of the one-level geometry g at the given
+// offsets ([n_tiles][2]); the tile index becomes an untransformed third axis
+// (no padding, no lag), and every antenna position o_j + A m must be unique.
+omni_status tile_geometry(Geometry& g, int64_t n_tiles, const double* offsets) {
+    if (g.D != 2) return fail(OMNI_ERR_INVALID_ARG, "a tile is one level");
+    std::vector<double> r;
+    positions(g, r);
+    const int64_t M = g.N;
+    std::vector<double> all(2 * M * n_tiles);
+    for (int64_t j = 0; j < n_tiles; ++j) {
+        if (!std::isfinite(offsets[2 * j]) || !std::isfinite(offsets[2 * j + 1]))
+            return fail(OMNI_ERR_INVALID_ARG, "tile %lld offset is not finite", (long long)j);
+        for (int64_t a = 0; a < M; ++a) {
+            all[2 * (j * M + a)] = offsets[2 * j] + r[2 * a];
+            all[2 * (j * M + a) + 1] = offsets[2 * j + 1] + r[2 * a + 1];
+        }
+    }
+    omni_status st = check_unique_positions(all, M * n_tiles);
+    if (st != OMNI_OK) return st;
+    g.D = 4;
+    g.n_levels = 2;
+    g.n[2] = (int32_t)n_tiles;
+    g.n[3] = 1;
+    g.Lp[2] = g.Lp[3] = 1;
+    g.N = M * n_tiles;
+    g.Q *= n_tiles * n_tiles;
+    g.A.resize(8, 0.0);
+    return OMNI_OK;
+}
+
 // Sec. II.D requires the map from r to the index set to be unique: reject two
 // antennas closer than 1e-9 max|r| (exactly coincident when max|r| = 0).
 // Spatial hash with cells of the tolerance size; each point checks the 3x3
@@ -135,8 +159,13 @@ omni_status check_unique(const Geometry& g) {
     if (g.N < 2) return OMNI_OK;
     std::vector<double> r;
     positions(g, r);
+    return check_unique_positions(r, g.N);
+}
+
+omni_status check_unique_positions(const std::vector<double>& r, int64_t N) {
+    if (N < 2) return OMNI_OK;
     double rmax = 0.0;
-    for (int64_t i = 0; i < g.N; ++i) rmax = std::max(rmax, std::hypot(r[2 * i], r[2 * i + 1]));
+    for (int64_t i = 0; i < N; ++i) rmax = std::max(rmax, std::hypot(r[2 * i], r[2 * i + 1]));
     const double tol = 1e-9 * rmax;
     const double cell = tol > 0.0 ? tol : 1.0;
     struct Key {
@@ -149,8 +178,8 @@ omni_status check_unique(const Geometry& g) {
         }
     };
     std::unordered_map<Key, std::vector<int64_t>, KeyHash> grid;
-    grid.reserve((size_t)g.N * 2);
-    for (int64_t i = 0; i < g.N; ++i) {
+    grid.reserve((size_t)N * 2);
+    for (int64_t i = 0; i < N; ++i) {
         const Key k{(int64_t)std::floor(r[2 * i] / cell), (int64_t)std::floor(r[2 * i + 1] / cell)};
         for (int64_t dx = -1; dx <= 1; ++dx)
             for (int64_t dy = -1; dy <= 1; ++dy) {
@@ -184,6 +213,8 @@ struct omni_plan {
     int64_t Cc = 1, Tc = 1;   // forward chunk: channels x samples
     int64_t chunk_mb = 1536;  // target size of each chunk scratch buffer
     bool beams = false;       // beam-space plan: level-1 axes unpadded, no lag over them
+    int64_t n_tiles = 0;      // tile-hybrid plan: identical tiles at arbitrary offsets
+    double inv_scale = 1.0;   // 1 / (points of the inverse transform)
     int64_t Cv = 1;           // inverse batch: channels
     int64_t fwd_elems = 0;    // float2 per sample, largest non-final forward output
     int64_t inv_elems = 0;    // float2 per channel, largest non-final inverse output
@@ -281,10 +312,17 @@ void choose_level(Pass& p) {
     p.W = p.inner == 1 ? 1 : 256 * lpt / p.L;
 }
 
+// FP64 values of one channel's accumulator: |F|^2 over the padded lattice, or
+// for a tile-hybrid plan the complex cross-spectra [n_tiles][n_tiles][L1 L2].
+int64_t acc_doubles(const omni_plan* pl) {
+    if (pl->n_tiles) return 2 * pl->n_tiles * pl->n_tiles * (int64_t)pl->g.Lp[0] * pl->g.Lp[1];
+    return pl->g.L;
+}
+
 omni_status build_passes(omni_plan* pl) {
     const Geometry& g = pl->g;
     std::vector<int> axes;
-    for (int d = 0; d < g.D; ++d)
+    for (int d = 0; d < (pl->n_tiles ? 2 : g.D); ++d)
         if (g.Lp[d] > 1) axes.push_back(d);
     if (axes.empty()) axes.push_back(0);  // a single antenna: an identity "transform"
     // forward: increasing axis order; inputs [outer n_e>d][n_d][inner L_e<d].
@@ -347,7 +385,7 @@ omni_status build_passes(omni_plan* pl) {
         p.outer = 1;
         for (int e = 0; e < d; ++e) p.inner *= g.Lp[e];
         for (int e = last_axis + 1; e < g.D; ++e) p.outer *= g.n[e];
-        p.mode = (k + 1 == stages.size()) ? MODE_LAST : MODE_MID;
+        p.mode = (k + 1 == stages.size() && !pl->n_tiles) ? MODE_LAST : MODE_MID;
         if (level) {
             choose_level(p);
         } else {
@@ -359,7 +397,21 @@ omni_status build_passes(omni_plan* pl) {
         if (p.mode == MODE_MID) pl->fwd_elems = std::max(pl->fwd_elems, p.outer * p.q_out * p.inner);
         pl->fwd.push_back(p);
     }
+    if (pl->n_tiles) {
+        // tile hybrid: cross-spectra of every tile pair, per frequency of the tile
+        Pass x{};
+        x.axis = 0;
+        x.kind = KIND_XSPEC;
+        x.mode = MODE_LAST;
+        x.L = g.Lp[0] * g.Lp[1];
+        x.n = (int)pl->n_tiles;
+        x.outer = pl->n_tiles;
+        x.inner = 1;
+        x.q_out = x.L;
+        pl->fwd.push_back(x);
+    }
     // inverse: decreasing axis order; inputs [outer Q_e>d][L_d][inner L_e<d]
+    // (tile hybrid: [tile pair][L2][L1], the pair index outermost)
     pl->inv.clear();
     pl->inv_elems = 0;
     std::vector<int> inv_axes;
@@ -378,12 +430,16 @@ omni_status build_passes(omni_plan* pl) {
         p.inner = 1;
         p.outer = 1;
         for (int e = 0; e < d; ++e) p.inner *= g.Lp[e];
-        for (int e = d + 1; e < g.D; ++e) p.outer *= 2 * g.n[e] - 1;
+        for (int e = d + 1; e < (pl->n_tiles ? 2 : g.D); ++e) p.outer *= 2 * g.n[e] - 1;
+        if (pl->n_tiles) p.outer *= pl->n_tiles * pl->n_tiles;
         p.mode = (a == 0) ? MODE_INV_LAST : MODE_INV_MID;
         choose_kind(p);
         if (p.mode == MODE_INV_MID) pl->inv_elems = std::max(pl->inv_elems, p.outer * p.q_out * p.inner);
         pl->inv.push_back(p);
     }
+    double inv_points = 1.0;
+    for (int d : inv_axes) inv_points *= (double)g.Lp[d];
+    pl->inv_scale = 1.0 / inv_points;
     // direct-DFT twiddle tables w_L^m, m < L, computed in double
     for (auto* list : {&pl->fwd, &pl->inv})
         for (Pass& p : *list) {
@@ -422,6 +478,7 @@ void choose_chunks(omni_plan* pl) {
         case KIND_TC5_B:
         case KIND_SMEM: ctas = (last.inner + last.W - 1) / last.W; break;
         case KIND_REG: ctas = (last.inner + 255) / 256; break;
+        case KIND_XSPEC: ctas = xspec_ctas_per_channel(last); break;
         default: ctas = (last.L * last.inner + 255) / 256; break;
     }
     // resident CTA slots of the GPU for that kernel
@@ -431,6 +488,7 @@ void choose_chunks(omni_plan* pl) {
     if (last.kind == KIND_LEVEL && level_last_occupancy(last, first_src, &per_sm) != cudaSuccess) per_sm = 0;
     if (last.kind == KIND_TC_B && tc_occupancy(KIND_TC_B, &per_sm) != cudaSuccess) per_sm = 0;
     if (last.kind == KIND_TC5_B && tc5_occupancy(&per_sm) != cudaSuccess) per_sm = 0;
+    if (last.kind == KIND_XSPEC && xspec_occupancy(&per_sm) != cudaSuccess) per_sm = 0;
     cudaGetLastError();
     int64_t slots = (int64_t)std::max(sms, 1) * std::max(per_sm, 2);
     if (sms <= 0) slots = 304;
@@ -501,7 +559,8 @@ void release(omni_plan* pl) {
 
 const char* kind_name(int k) {
     return k == KIND_REG ? "reg" : k == KIND_SMEM ? "smem" : k == KIND_LEVEL ? "level"
-         : k == KIND_TC_A || k == KIND_TC_B ? "tc" : k == KIND_TC5_B ? "tcgen05-" : "direct";
+         : k == KIND_TC_A || k == KIND_TC_B ? "tc" : k == KIND_TC5_B ? "tcgen05-"
+         : k == KIND_XSPEC ? "xspec" : "direct";
 }
 const char* mode_name(int m) {
     return m == MODE_MID ? "mid" : m == MODE_LAST ? "last" : m == MODE_INV_MID ? "mid" : "last";
@@ -547,6 +606,8 @@ double src_bytes(int src_kind) {
 
 // Algorithmic bytes of one launch: inputs read plus outputs written.
 double pass_bytes(const Pass& p, const PassArgs& a) {
+    if (p.kind == KIND_XSPEC)  // every tile's spectrum once; the FP64 complex fold read and written
+        return (double)a.S * a.tc * p.outer * p.L * 8.0 + (double)a.S * p.outer * p.outer * p.L * 32.0;
     const double in = src_bytes(a.src_kind);
     const bool two_axes = p.kind == KIND_LEVEL || p.kind == KIND_TC_A || p.kind == KIND_TC_B ||
                           p.kind == KIND_TC5_B;
@@ -568,6 +629,8 @@ double pass_flops(const Pass& p, const PassArgs& a) {
     const double lg = std::log2((double)std::max(p.L, 2));
     const double line = 5.0 * p.L * lg;
     switch (p.kind) {
+        case KIND_XSPEC:  // one complex multiply-add per tile pair, frequency and sample
+            return (double)a.S * a.tc * p.outer * p.outer * p.L * 8.0;
         case KIND_TC_A:  // per 16x16 block: 32 + 96 products
             return (double)a.S * p.outer * 128.0 * 4096.0;
         case KIND_TC_B:  // per level-1 frequency and sample: 6 + 12 products, |F|^2
@@ -625,7 +688,7 @@ omni_status run_chunk(omni_plan* pl, const void* volts, int64_t vc0, int64_t Tsr
         a.tc = (int)tc;
         a.c0 = c0;
         a.P = pl->P;
-        a.P_stride = pl->g.L;
+        a.P_stride = acc_doubles(pl);
         a.err = pl->dev_err;
         a.force_expire = pl->force_expire;
         float2* dst = pl->buf[slot >= 0 ? slot : (int)(k & 1)];
@@ -684,8 +747,8 @@ omni_status run_inverse(omni_plan* pl, double2* V, cudaStream_t st) {
     for (int64_t c0 = 0; c0 < pl->C; c0 += pl->Cv) {
         const int64_t cv = std::min(pl->Cv, pl->C - c0);
         const void* src = pl->P;
-        int src_kind = SRC_P64;
-        int64_t src_stride = pl->g.L;
+        int src_kind = pl->n_tiles ? SRC_PC64 : SRC_P64;
+        int64_t src_stride = pl->n_tiles ? acc_doubles(pl) / 2 : pl->g.L;
         for (size_t k = 0; k < pl->inv.size(); ++k) {
             const Pass& p = pl->inv[k];
             PassArgs a{};
@@ -699,7 +762,7 @@ omni_status run_inverse(omni_plan* pl, double2* V, cudaStream_t st) {
             if (p.mode == MODE_INV_LAST) {
                 a.V = V;
                 a.V_stride = pl->g.Q;
-                a.scale = 1.0 / inverse_length(pl->g, pl->beams);
+                a.scale = pl->inv_scale;
             } else {
                 a.dst = dst;
                 a.dst_stride = p.outer * p.q_out * p.inner;
@@ -851,7 +914,8 @@ omni_status omni_unique_baselines(const omni_level* levels, int n_levels, int64_
 
 static omni_status create_plan(const omni_level* levels, int n_levels, int64_t n_channels,
                                omni_dtype dtype, omni_precision precision, int64_t chunk_mb,
-                               omni_plan** out, bool beams = false);
+                               omni_plan** out, bool beams = false, int64_t n_tiles = 0,
+                               const double* tile_offsets = nullptr);
 
 omni_status omni_plan_create(const omni_level* levels, int n_levels, int64_t n_channels,
                              omni_dtype dtype, omni_precision precision, omni_plan** out) {
@@ -863,9 +927,18 @@ omni_status omni_plan_create_beams(const omni_level* levels, int n_levels, int64
     return create_plan(levels, n_levels, n_channels, dtype, OMNI_FP32, 1536, out, true);
 }
 
+omni_status omni_plan_create_tiles(const omni_level* tile, int64_t n_tiles, const double* offsets,
+                                   int64_t n_channels, omni_dtype dtype, omni_plan** out) {
+    if (n_tiles < 1) return fail(OMNI_ERR_INVALID_ARG, "n_tiles must be >= 1");
+    if (!offsets) return fail(OMNI_ERR_INVALID_ARG, "offsets is NULL");
+    if (n_tiles > 4096) return fail(OMNI_ERR_UNSUPPORTED, "at most 4096 tiles");
+    return create_plan(tile, 1, n_channels, dtype, OMNI_FP32, 1536, out, false, n_tiles, offsets);
+}
+
 static omni_status create_plan(const omni_level* levels, int n_levels, int64_t n_channels,
                                omni_dtype dtype, omni_precision precision, int64_t chunk_mb,
-                               omni_plan** out, bool beams) {
+                               omni_plan** out, bool beams, int64_t n_tiles,
+                               const double* tile_offsets) {
     if (!out) return fail(OMNI_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (n_channels < 1) return fail(OMNI_ERR_INVALID_ARG, "n_channels must be >= 1");
@@ -876,10 +949,13 @@ static omni_status create_plan(const omni_level* levels, int n_levels, int64_t n
         return fail(OMNI_ERR_UNSUPPORTED, "beam-space plans run the FP32 path");
     if (beams && levels && n_levels < 2)
         return fail(OMNI_ERR_UNSUPPORTED, "a beam-space plan needs at least two levels");
+    if (n_tiles && precision != OMNI_FP32)
+        return fail(OMNI_ERR_UNSUPPORTED, "tile-hybrid plans run the FP32 path");
     omni_plan* pl = new omni_plan();
     pl->beams = beams;
+    pl->n_tiles = n_tiles;
     omni_status st = make_geometry(levels, n_levels, pl->g, beams);
-    if (st == OMNI_OK) st = check_unique(pl->g);
+    if (st == OMNI_OK) st = n_tiles ? tile_geometry(pl->g, n_tiles, tile_offsets) : check_unique(pl->g);
     if (st != OMNI_OK) {
         delete pl;
         return st;
@@ -977,7 +1053,7 @@ static omni_status create_plan(const omni_level* levels, int n_levels, int64_t n
     }
     init_stats(pl);
     const size_t buf_bytes = (size_t)std::max<int64_t>(1, pl->buf_elems) * sizeof(float2);
-    const size_t P_bytes = (size_t)pl->C * pl->g.L * sizeof(double);
+    const size_t P_bytes = (size_t)pl->C * acc_doubles(pl) * sizeof(double);
     if ((e = cudaMalloc(&pl->buf[0], buf_bytes)) != cudaSuccess ||
         (e = cudaMalloc(&pl->buf[1], buf_bytes)) != cudaSuccess ||
         (e = cudaMalloc(&pl->P, P_bytes)) != cudaSuccess ||
@@ -1218,7 +1294,7 @@ omni_status omni_visibilities(omni_plan* pl, double* vis_dev, int reset, void* s
     cudaStream_t s = (cudaStream_t)stream;
     st = run_inverse(pl, reinterpret_cast<double2*>(vis_dev), s);
     if (st != OMNI_OK) return st;
-    if (reset) OMNI_CUDA(cudaMemsetAsync(pl->P, 0, (size_t)pl->C * pl->g.L * sizeof(double), s), "cudaMemsetAsync");
+    if (reset) OMNI_CUDA(cudaMemsetAsync(pl->P, 0, (size_t)pl->C * acc_doubles(pl) * sizeof(double), s), "cudaMemsetAsync");
     OMNI_CUDA(cudaStreamSynchronize(s), "device error during correlation");
     return check_device_error(pl);
 }
@@ -1241,7 +1317,7 @@ omni_status omni_visibilities_host(omni_plan* pl, double* vis_host, int reset, v
     if (!pl->vis_tmp) OMNI_CUDA(cudaMalloc(&pl->vis_tmp, bytes), "cudaMalloc(visibility staging)");
     st = run_inverse(pl, pl->vis_tmp, s);
     if (st != OMNI_OK) return st;
-    if (reset) OMNI_CUDA(cudaMemsetAsync(pl->P, 0, (size_t)pl->C * pl->g.L * sizeof(double), s), "cudaMemsetAsync");
+    if (reset) OMNI_CUDA(cudaMemsetAsync(pl->P, 0, (size_t)pl->C * acc_doubles(pl) * sizeof(double), s), "cudaMemsetAsync");
     OMNI_CUDA(cudaMemcpyAsync(vis_host, pl->vis_tmp, bytes, cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync(D2H)");
     OMNI_CUDA(cudaStreamSynchronize(s), "device error during correlation");
     return check_device_error(pl);
@@ -1256,7 +1332,7 @@ omni_status omni_reset(omni_plan* pl, void* stream) {
         return OMNI_OK;
     }
     DeviceGuard dg(pl->device);
-    OMNI_CUDA(cudaMemsetAsync(pl->P, 0, (size_t)pl->C * pl->g.L * sizeof(double), (cudaStream_t)stream),
+    OMNI_CUDA(cudaMemsetAsync(pl->P, 0, (size_t)pl->C * acc_doubles(pl) * sizeof(double), (cudaStream_t)stream),
               "cudaMemsetAsync");
     return OMNI_OK;
 }

@@ -113,7 +113,7 @@ __device__ __forceinline__ void fft_dif(float2 (&v)[L]) {
 __device__ __forceinline__ int64_t src_base(const PassArgs& a, int64_t s) {
     if (a.src_kind == SRC_CF32 || a.src_kind == SRC_CI8)
         return ((a.vc0 + s / a.tc) * a.T + a.t0 + s % a.tc) * a.N;
-    if (a.src_kind == SRC_P64) return (a.c0 + s) * a.src_stride;
+    if (a.src_kind == SRC_P64 || a.src_kind == SRC_PC64) return (a.c0 + s) * a.src_stride;
     return s * a.src_stride;
 }
 
@@ -124,6 +124,12 @@ __device__ __forceinline__ float2 ld_src(const void* p, int64_t e) {
     } else if constexpr (SRC == SRC_CI8) {
         const char2 c = reinterpret_cast<const char2*>(p)[e];
         return make_float2((float)c.x, (float)c.y);
+    } else if constexpr (SRC == SRC_PC64) {
+        // conjugated on load: the inverse passes run forward (e^-) transforms and
+        // conjugate at the end, IFFT(S) = conj(FFT(conj(S))) / L; a real |F|^2
+        // needs no input conjugate, a complex cross-spectrum does
+        const double2 d = __ldg(reinterpret_cast<const double2*>(p) + e);
+        return make_float2((float)d.x, -(float)d.y);
     } else {
         return make_float2((float)__ldg(reinterpret_cast<const double*>(p) + e), 0.0f);
     }
@@ -137,8 +143,8 @@ __device__ __forceinline__ int inv_bin(int q, int q_shift, int L) {
 }
 
 // Source kinds a pass mode can read: forward passes read the caller's
-// voltages or the scratch buffer, inverse passes the FP64 accumulator or the
-// scratch buffer.
+// voltages or the scratch buffer, inverse passes the FP64 accumulator (real
+// |F|^2, or complex cross-spectra of the tile hybrid) or the scratch buffer.
 template <int MODE, class F>
 cudaError_t dispatch_src(int src_kind, F&& f) {
     if constexpr (MODE == MODE_MID || MODE == MODE_LAST) {
@@ -152,6 +158,7 @@ cudaError_t dispatch_src(int src_kind, F&& f) {
         switch (src_kind) {
             case SRC_BUF: return f(std::integral_constant<int, SRC_BUF>{});
             case SRC_P64: return f(std::integral_constant<int, SRC_P64>{});
+            case SRC_PC64: return f(std::integral_constant<int, SRC_PC64>{});
             default: return cudaErrorInvalidValue;
         }
     }

@@ -14,7 +14,8 @@ enum SrcKind : int {
     SRC_BUF = 0,   // float2 scratch buffer written by the previous pass
     SRC_CF32 = 1,  // caller voltages, complex float32 [.][T][N]
     SRC_CI8 = 2,   // caller voltages, complex int8   [.][T][N]
-    SRC_P64 = 3    // FP64 |F|^2 accumulator [C][L] (real), inverse passes
+    SRC_P64 = 3,   // FP64 |F|^2 accumulator [C][L] (real), inverse passes
+    SRC_PC64 = 4   // FP64 complex cross-spectrum accumulator (re, im), tile-hybrid inverse
 };
 
 // What a pass does with the transformed lines.
@@ -33,7 +34,8 @@ enum PassKind : int {
     KIND_LEVEL = 3,  // both axes of one square level (L_a = L_b <= 64) in shared memory
     KIND_TC_A = 4,   // mixed precision, finest level as split-FP16 tensor-core GEMMs
     KIND_TC_B = 5,   // mixed precision, coarse level + |F|^2 as tensor-core GEMMs (LAST, mma.sync)
-    KIND_TC5_B = 6   // the same on 5th-generation tensor cores (tcgen05, tensor memory)
+    KIND_TC5_B = 6,  // the same on 5th-generation tensor cores (tcgen05, tensor memory)
+    KIND_XSPEC = 7   // tile hybrid: cross-spectra of every tile pair summed over samples (LAST)
 };
 
 // One axis transform.  The data of one sample (or channel) is viewed as
@@ -95,6 +97,11 @@ bool tc_supports(const int32_t* n, int D, int dtype_is_ci8);
 cudaError_t upload_tc_tables();
 cudaError_t tc_occupancy(int kind, int* blocks_per_sm);
 int tc_stage_b_tile();  // level-1 frequencies per stage-B CTA
+
+// Tile hybrid: cross-spectrum accumulation between the tiles' padded spectra.
+cudaError_t launch_xspec(const Pass& p, const PassArgs& a, cudaStream_t stream);
+cudaError_t xspec_occupancy(int* blocks_per_sm);
+int64_t xspec_ctas_per_channel(const Pass& p);
 cudaError_t launch_tc(const Pass& p, const PassArgs& a, cudaStream_t stream);
 cudaError_t upload_tc5_tables();
 cudaError_t tc5_occupancy(int* blocks_per_sm);

@@ -1,0 +1,94 @@
+// omni_tiles.cu -- tile hybrid (Sec. III): FFT correlation within identical
+// tiles placed at arbitrary offsets, brute-force correlation between them.
+//
+// After the forward passes each sample holds every tile's zero-padded 2-D
+// spectrum Y_j(k), k = k1 + L1 k2 (the tile's "synthesized beams").  This pass
+// accumulates, for every ordered tile pair (i, j) and frequency k,
+//   S_ij(k) += sum over the chunk's samples of Y_i(k) conj(Y_j(k)),
+// in FP32 registers over the chunk, then in an FP64 complex accumulator
+// [C][n_tiles][n_tiles][K].  The inverse 2-D FFT of S_ij gives the visibility
+// of every antenna pair (a in tile i, b in tile j) with intra-tile offset
+// m_a - m_b = D: the convolution theorem of Sec. II.C applied to two
+// different tiles, exact because of the padding.
+#include "omni_fft_common.cuh"
+
+namespace omni {
+namespace {
+
+constexpr int kXK = 32;  // frequencies per CTA
+constexpr int kXI = 16;  // tiles i per CTA (one per warp)
+constexpr int kXJ = 16;  // tiles j per thread
+
+// CTA = (channel of the chunk, tile group i, tile chunk j, frequency tile);
+// thread = (frequency, tile i), 16 complex accumulators (tiles j).
+__global__ void __launch_bounds__(kXK * kXI) xspec(Pass p, PassArgs a) {
+    __shared__ float2 sI[kXI][kXK];
+    __shared__ float2 sJ[kXJ][kXK];
+    const int NT = (int)p.outer;
+    const int64_t K = p.L;
+    const int64_t ktiles = (K + kXK - 1) / kXK;
+    const int igroups = (NT + kXI - 1) / kXI, jchunks = (NT + kXJ - 1) / kXJ;
+    int64_t b = blockIdx.x;
+    const int64_t kt = b % ktiles;
+    b /= ktiles;
+    const int jc = (int)(b % jchunks);
+    b /= jchunks;
+    const int ig = (int)(b % igroups);
+    const int64_t cc = b / igroups;
+    const int kl = threadIdx.x % kXK, il = threadIdx.x / kXK;
+    const int64_t k = kt * kXK + kl;
+    const int i = ig * kXI + il, j0 = jc * kXJ;
+    float ar[kXJ], ai[kXJ];
+#pragma unroll
+    for (int jj = 0; jj < kXJ; ++jj) ar[jj] = ai[jj] = 0.f;
+    for (int ts = 0; ts < a.tc; ++ts) {
+        const float2* Y = reinterpret_cast<const float2*>(a.src) + src_base(a, cc * a.tc + ts);
+        {
+            const int64_t kk = kt * kXK + kl;
+            const bool ok = i < NT && kk < K;
+            sI[il][kl] = ok ? __ldg(Y + (int64_t)i * K + kk) : make_float2(0.f, 0.f);
+            const int jr = j0 + il;
+            sJ[il][kl] = (jr < NT && kk < K) ? __ldg(Y + (int64_t)jr * K + kk) : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        const float2 y = sI[il][kl];
+#pragma unroll
+        for (int jj = 0; jj < kXJ; ++jj) {
+            const float2 z = sJ[jj][kl];
+            ar[jj] = fmaf(y.x, z.x, fmaf(y.y, z.y, ar[jj]));   // y conj(z)
+            ai[jj] = fmaf(y.y, z.x, fmaf(-y.x, z.y, ai[jj]));
+        }
+        __syncthreads();
+    }
+    if (i >= NT || k >= K) return;
+    double2* S = reinterpret_cast<double2*>(a.P + (a.c0 + cc) * a.P_stride);
+#pragma unroll
+    for (int jj = 0; jj < kXJ; ++jj) {
+        const int j = j0 + jj;
+        if (j >= NT) break;
+        double2& s = S[((int64_t)i * NT + j) * K + k];
+        s.x += (double)ar[jj];
+        s.y += (double)ai[jj];
+    }
+}
+
+}  // namespace
+
+int64_t xspec_ctas_per_channel(const Pass& p) {
+    const int64_t NT = p.outer;
+    return ((p.L + kXK - 1) / kXK) * ((NT + kXI - 1) / kXI) * ((NT + kXJ - 1) / kXJ);
+}
+
+cudaError_t xspec_occupancy(int* blocks_per_sm) {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, xspec, kXK * kXI, 0);
+}
+
+cudaError_t launch_xspec(const Pass& p, const PassArgs& a, cudaStream_t st) {
+    if (a.src_kind != SRC_BUF) return cudaErrorInvalidValue;
+    const int64_t blocks = a.S * xspec_ctas_per_channel(p);
+    if (blocks <= 0) return cudaSuccess;
+    xspec<<<(unsigned)blocks, kXK * kXI, 0, st>>>(p, a);
+    return cudaGetLastError();
+}
+
+}  // namespace omni

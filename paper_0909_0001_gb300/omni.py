@@ -33,7 +33,7 @@ EXPORTS = (
     "omni_visibilities_host", "omni_reset", "omni_sync", "omni_last_error",
     "omni_status_string", "omni_profile_enable", "omni_profile_read", "omni_correlate_noalloc",
     "omni_plan_create_batch", "omni_batch_info", "omni_radial_bins", "omni_unique_baselines",
-    "omni_sum_groups", "omni_plan_create_beams",
+    "omni_sum_groups", "omni_plan_create_beams", "omni_plan_create_tiles",
 )
 
 
@@ -73,6 +73,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "omni_plan_create": (ctypes.c_int, [lv, ctypes.c_int, i64, ctypes.c_int, ctypes.c_int,
                                             P(vp)]),
         "omni_plan_create_beams": (ctypes.c_int, [lv, ctypes.c_int, i64, ctypes.c_int, P(vp)]),
+        "omni_plan_create_tiles": (ctypes.c_int, [lv, i64, P(dbl), i64, ctypes.c_int, P(vp)]),
         "omni_plan_destroy": (None, [vp]),
         "omni_plan_info": (ctypes.c_int, [vp, P(ctypes.c_int), P(i32), P(i32), P(i64), P(i64),
                                           P(i64)]),
@@ -347,6 +348,35 @@ class BeamPlan(Plan):
 
     def split(self, V: torch.Tensor) -> torch.Tensor:
         return V.reshape(self.channels, self.n_coarse_lags, self.beam_shape[1], self.beam_shape[0])
+
+
+class TilePlan(Plan):
+    """Tile hybrid (Sec. III): identical one-level tiles at arbitrary offsets,
+    FFT-correlated within each tile and pairwise between tiles.  visibilities()
+    returns [C][n_tiles * n_tiles * Q] complex128; split() views it as
+    [C][i][j][Q] (lags of baselines([tile]) order)."""
+
+    def __init__(self, tile: Level, offsets, channels: int, dtype: str = "cf32"):
+        self.offsets = np.ascontiguousarray(np.asarray(offsets, dtype=np.float64).reshape(-1, 2))
+        self.n_tiles = int(self.offsets.shape[0])
+        super().__init__([tile], channels, dtype=dtype, precision="fp32")
+        self.n_tile_lags = self.n_lags // (self.n_tiles * self.n_tiles)
+
+    def _create(self) -> ctypes.c_void_p:
+        h = ctypes.c_void_p()
+        off = self.offsets.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        _check(load().omni_plan_create_tiles(_levels(self.levels), self.n_tiles, off,
+                                             self.channels, DTYPES[self.dtype], ctypes.byref(h)))
+        return h
+
+    def split(self, V: torch.Tensor) -> torch.Tensor:
+        return V.reshape(self.channels, self.n_tiles, self.n_tiles, self.n_tile_lags)
+
+    def baseline_vectors(self) -> np.ndarray:
+        """Physical baseline o_i - o_j + A D of every output, [n_tiles][n_tiles][Q][2]."""
+        _, _, dr = baselines(self.levels)
+        o = self.offsets
+        return (o[:, None, None, :] - o[None, :, None, :]) + dr[None, None, :, :]
 
 
 class BatchPlan(Plan):

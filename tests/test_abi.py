@@ -139,3 +139,16 @@ def test_epilogue_rejects_bad_arguments(lib):
     with pytest.raises(omni.OmniError):
         omni.radial_bins([synth.Level(4, 4)], 0.0, 10)
     assert lib.omni_sum_groups(None, 1, 1, None, 1, None, None) == 1
+
+
+def test_tile_plans_check_geometry_without_a_gpu(lib):
+    tile = synth.Level(4, 4, (1.0, 0.0, 0.0, 1.0))
+    with pytest.raises(omni.OmniError) as e:     # tile 1 overlaps tile 0 exactly
+        omni.TilePlan(tile, [[0.0, 0.0], [2.0, 1.0]], 1)
+    assert e.value.status == 2
+    with pytest.raises(omni.OmniError) as e:
+        omni.TilePlan(tile, [[0.0, 0.0], [float("nan"), 1.0]], 1)
+    assert e.value.status == 1
+    with pytest.raises(omni.OmniError) as e:
+        omni.TilePlan(tile, np.zeros((0, 2)), 1)
+    assert e.value.status == 1
