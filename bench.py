@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-direct", action="store_true", help="skip the direct N^2 context run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-beams", action="store_true", help="skip the beam-space variant")
+    ap.add_argument("--no-tiles", action="store_true", help="skip the tile-hybrid variant")
     return ap.parse_args()
 
 
@@ -484,6 +486,53 @@ def run_ours(args):
                "ms_per_step": e2e_s * 1e3, "steps": n_e2e}
         del xh, vh
 
+    # beam-space variant (Appendix A steps 4-5) on the same voltages, FP32 path
+    beams = None
+    if rank == 0 and len(w.levels) >= 2 and not args.no_beams:
+        bp = omni.BeamPlan(w.levels, w.channels, dtype=w.dtype)
+        bvis = torch.empty((w.channels, bp.n_lags), dtype=torch.complex128, device="cuda")
+        ms_b, bstats = timed_steps(bp, x, bvis, max(2, min(args.steps, 5)), 3, stream,
+                                   lambda: None, True)
+        beams = {"value": units / (ms_b * 1e-3), "unit": UNIT, "ms_per_step": ms_b,
+                 "pointings": bp.n_beams, "coarse_lags": bp.n_coarse_lags,
+                 "kernels": [{k: st[k] for k in ("name", "launches", "total_ms")}
+                             for st in bstats if st["launches"]]}
+        bp.close()
+        del bvis
+
+    # tile hybrid (Sec. III) on the same voltages: the level-1 blocks as tiles at
+    # their level-2 positions, correlated pairwise by brute force; on this
+    # lattice, summing tile pairs with equal grid offsets must give back the
+    # hypercube's visibilities
+    tiles = None
+    if rank == 0 and len(w.levels) == 2 and not args.no_tiles:
+        lv1, lv2 = w.levels
+        A2 = np.array(lv2.A, dtype=np.float64).reshape(2, 2)
+        grid = np.array([(j1, j2) for j2 in range(lv2.n2) for j1 in range(lv2.n1)], dtype=np.float64)
+        offs = grid @ A2.T
+        tp = omni.TilePlan(lv1, offs, w.channels, dtype=w.dtype)
+        tvis = torch.empty((w.channels, tp.n_lags), dtype=torch.complex128, device="cuda")
+        ms_t, tstats = timed_steps(tp, x, tvis, 2, 3, stream, lambda: None, True)
+        # regroup channel 0 by (intra-tile lag, tile-grid lag) and compare
+        Vt = tp.split(tvis)[0]                                   # [i][j][Q1 Q2]
+        N1, N2 = lv2.n1, lv2.n2
+        gi = torch.arange(tp.n_tiles, device="cuda")
+        d1 = (gi % N1)[:, None] - (gi % N1)[None, :] + (N1 - 1)
+        d2 = (gi // N1)[:, None] - (gi // N1)[None, :] + (N2 - 1)
+        dg = (d1 + (2 * N1 - 1) * d2).reshape(-1)                    # tile-grid lag index
+        acc = torch.zeros(((2 * N1 - 1) * (2 * N2 - 1), tp.n_tile_lags), dtype=torch.complex128,
+                          device="cuda")
+        acc.index_add_(0, dg, Vt.reshape(-1, tp.n_tile_lags))
+        hyp = vis[0]
+        diff = float((acc.reshape(-1) - hyp).abs().norm() / hyp.abs().norm())
+        tiles = {"value": units / (ms_t * 1e-3), "unit": UNIT, "ms_per_step": ms_t,
+                 "tiles": tp.n_tiles, "pairs": tp.n_tiles ** 2,
+                 "rel_diff_vs_hypercube_ch0": diff,
+                 "kernels": [{k: st[k] for k in ("name", "launches", "total_ms")}
+                             for st in tstats if st["launches"]]}
+        tp.close()
+        del tvis, acc
+
     n2 = None
     if rank == 0 and not args.no_direct and w.n_antennas <= 16384:
         # one channel of the same step's voltages (its visibilities are vis[0])
@@ -510,7 +559,8 @@ def run_ours(args):
                                      w.channels * w.samples * args.steps, serial),
                 "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": sum(s["launches"] for s in stats),
-                "clocks": clocks, "epilogue": epilogue, "direct_n2": n2,
+                "clocks": clocks, "epilogue": epilogue, "direct_n2": n2, "beam_space": beams,
+                "tile_hybrid": tiles,
                 "kernels": [{k: s[k] for k in ("name", "launches", "total_ms")}
                             for s in stats if s["launches"]]}
         if "fp32" in results and args.precision != "fp32":

@@ -110,10 +110,13 @@ __device__ __forceinline__ void fft_dif(float2 (&v)[L]) {
 // ---------------------------------------------------------------- sources
 
 // Offset of sample s's first element in the source, in source elements.
+// (Kept to one comparison per branch: a second one here raised the tensor-core
+// stage-A kernel from 80 to 82 registers, past an allocation step, and cost 9%
+// of the mixed path's step time through lost co-residency.)
 __device__ __forceinline__ int64_t src_base(const PassArgs& a, int64_t s) {
     if (a.src_kind == SRC_CF32 || a.src_kind == SRC_CI8)
         return ((a.vc0 + s / a.tc) * a.T + a.t0 + s % a.tc) * a.N;
-    if (a.src_kind == SRC_P64 || a.src_kind == SRC_PC64) return (a.c0 + s) * a.src_stride;
+    if (a.src_kind >= SRC_P64) return (a.c0 + s) * a.src_stride;  // P64, PC64: per channel
     return s * a.src_stride;
 }
 

@@ -15,13 +15,15 @@
 namespace omni {
 namespace {
 
-constexpr int kXK = 32;  // frequencies per CTA
-constexpr int kXI = 16;  // tiles i per CTA (one per warp)
-constexpr int kXJ = 16;  // tiles j per thread
+constexpr int kXK = 32;  // frequencies per CTA (one per lane)
+constexpr int kXR = 8;   // thread rows per CTA (warps)
+constexpr int kXI = 16;  // tiles i per CTA: two per thread (rows r and r + 8)
+constexpr int kXJ = 16;  // tiles j per CTA, all of them per thread
 
 // CTA = (channel of the chunk, tile group i, tile chunk j, frequency tile);
-// thread = (frequency, tile i), 16 complex accumulators (tiles j).
-__global__ void __launch_bounds__(kXK * kXI) xspec(Pass p, PassArgs a) {
+// thread = (frequency, tiles i = r and r + 8), 2 x 16 complex accumulators:
+// each spectrum value read from shared memory feeds two (or sixteen) products.
+__global__ void __launch_bounds__(kXK * kXR, 2) xspec(Pass p, PassArgs a) {
     __shared__ float2 sI[kXI][kXK];
     __shared__ float2 sJ[kXJ][kXK];
     const int NT = (int)p.outer;
@@ -35,40 +37,49 @@ __global__ void __launch_bounds__(kXK * kXI) xspec(Pass p, PassArgs a) {
     b /= jchunks;
     const int ig = (int)(b % igroups);
     const int64_t cc = b / igroups;
-    const int kl = threadIdx.x % kXK, il = threadIdx.x / kXK;
+    const int kl = threadIdx.x % kXK, r = threadIdx.x / kXK;
     const int64_t k = kt * kXK + kl;
-    const int i = ig * kXI + il, j0 = jc * kXJ;
-    float ar[kXJ], ai[kXJ];
+    const int i0 = ig * kXI, j0 = jc * kXJ;
+    float ar[2][kXJ], ai[2][kXJ];
 #pragma unroll
-    for (int jj = 0; jj < kXJ; ++jj) ar[jj] = ai[jj] = 0.f;
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int jj = 0; jj < kXJ; ++jj) ar[h][jj] = ai[h][jj] = 0.f;
     for (int ts = 0; ts < a.tc; ++ts) {
         const float2* Y = reinterpret_cast<const float2*>(a.src) + src_base(a, cc * a.tc + ts);
-        {
-            const int64_t kk = kt * kXK + kl;
-            const bool ok = i < NT && kk < K;
-            sI[il][kl] = ok ? __ldg(Y + (int64_t)i * K + kk) : make_float2(0.f, 0.f);
-            const int jr = j0 + il;
-            sJ[il][kl] = (jr < NT && kk < K) ? __ldg(Y + (int64_t)jr * K + kk) : make_float2(0.f, 0.f);
+        const bool kin = k < K;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int ii = i0 + r + h * kXR, jr = j0 + r + h * kXR;
+            sI[r + h * kXR][kl] = (ii < NT && kin) ? __ldg(Y + (int64_t)ii * K + k) : make_float2(0.f, 0.f);
+            sJ[r + h * kXR][kl] = (jr < NT && kin) ? __ldg(Y + (int64_t)jr * K + k) : make_float2(0.f, 0.f);
         }
         __syncthreads();
-        const float2 y = sI[il][kl];
+        const float2 y0 = sI[r][kl], y1 = sI[r + kXR][kl];
 #pragma unroll
         for (int jj = 0; jj < kXJ; ++jj) {
             const float2 z = sJ[jj][kl];
-            ar[jj] = fmaf(y.x, z.x, fmaf(y.y, z.y, ar[jj]));   // y conj(z)
-            ai[jj] = fmaf(y.y, z.x, fmaf(-y.x, z.y, ai[jj]));
+            ar[0][jj] = fmaf(y0.x, z.x, fmaf(y0.y, z.y, ar[0][jj]));   // y conj(z)
+            ai[0][jj] = fmaf(y0.y, z.x, fmaf(-y0.x, z.y, ai[0][jj]));
+            ar[1][jj] = fmaf(y1.x, z.x, fmaf(y1.y, z.y, ar[1][jj]));
+            ai[1][jj] = fmaf(y1.y, z.x, fmaf(-y1.x, z.y, ai[1][jj]));
         }
         __syncthreads();
     }
-    if (i >= NT || k >= K) return;
+    if (k >= K) return;
     double2* S = reinterpret_cast<double2*>(a.P + (a.c0 + cc) * a.P_stride);
 #pragma unroll
-    for (int jj = 0; jj < kXJ; ++jj) {
-        const int j = j0 + jj;
-        if (j >= NT) break;
-        double2& s = S[((int64_t)i * NT + j) * K + k];
-        s.x += (double)ar[jj];
-        s.y += (double)ai[jj];
+    for (int h = 0; h < 2; ++h) {
+        const int i = i0 + r + h * kXR;
+        if (i >= NT) break;
+#pragma unroll
+        for (int jj = 0; jj < kXJ; ++jj) {
+            const int j = j0 + jj;
+            if (j >= NT) break;
+            double2& s = S[((int64_t)i * NT + j) * K + k];
+            s.x += (double)ar[h][jj];
+            s.y += (double)ai[h][jj];
+        }
     }
 }
 
@@ -80,14 +91,14 @@ int64_t xspec_ctas_per_channel(const Pass& p) {
 }
 
 cudaError_t xspec_occupancy(int* blocks_per_sm) {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, xspec, kXK * kXI, 0);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, xspec, kXK * kXR, 0);
 }
 
 cudaError_t launch_xspec(const Pass& p, const PassArgs& a, cudaStream_t st) {
     if (a.src_kind != SRC_BUF) return cudaErrorInvalidValue;
     const int64_t blocks = a.S * xspec_ctas_per_channel(p);
     if (blocks <= 0) return cudaSuccess;
-    xspec<<<(unsigned)blocks, kXK * kXI, 0, st>>>(p, a);
+    xspec<<<(unsigned)blocks, kXK * kXR, 0, st>>>(p, a);
     return cudaGetLastError();
 }
 

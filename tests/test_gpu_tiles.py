@@ -88,3 +88,25 @@ def test_tiles_hermitian_pairs_and_host_path():
             np.testing.assert_allclose(Vh[0, j, i][::-1], np.conj(Vh[0, i, j]), rtol=0,
                                        atol=1e-5 * np.abs(Vh).max())
             np.testing.assert_allclose(dr[j, i][::-1], -dr[i, j], rtol=0, atol=1e-9)
+
+
+def test_tiles_on_the_lattice_equal_the_hypercube():
+    """The 2-level workload's blocks as tiles at their level-2 positions: the
+    tile pairs with equal grid offset sum to the hypercube plan's visibilities."""
+    w = synth.workload("hier2")
+    lv1, lv2 = w.levels
+    x = synth.voltages(w, channels=2, samples=8)
+    A2 = np.array(lv2.A).reshape(2, 2)
+    grid = np.array([(j1, j2) for j2 in range(lv2.n2) for j1 in range(lv2.n1)], dtype=float)
+    Vt = tile_vis(lv1, grid @ A2.T, x, "ci8")                       # [C][i][j][Q]
+    with omni.Plan(w.levels, 2, dtype="ci8") as plan:
+        plan.correlate(x.cuda())
+        H = plan.visibilities().cpu().numpy()
+    N1, N2 = lv2.n1, lv2.n2
+    R1 = 2 * N1 - 1
+    acc = np.zeros((2, R1 * (2 * N2 - 1), Vt.shape[-1]), dtype=complex)
+    for i in range(N1 * N2):
+        for j in range(N1 * N2):
+            g = (i % N1 - j % N1 + N1 - 1) + R1 * (i // N1 - j // N1 + N2 - 1)
+            acc[:, g] += Vt[:, i, j]
+    assert relerr_per_channel(acc.reshape(2, -1), H) <= TOL
