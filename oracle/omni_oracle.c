@@ -381,6 +381,69 @@ void oracle_tile_correlate(int n1, int n2, int n_tiles, int64_t C, int64_t T, in
     }
 }
 
+/*
+ * F-engine (Appendix A, step 2: each antenna's samples Fourier transformed in
+ * time to separate the frequency channels, then calibrated), as a polyphase
+ * filter bank written out term by term.  Frame t of antenna a, with frame
+ * length 2F and P taps:
+ *
+ *   u_t(n)  = sum_{p < P} w(p 2F + n) r_a((t + p) 2F + n),        n < 2F,
+ *   X_t(f)  = sum_{n < 2F} u_t(n) exp(-2 pi i f n / (2F)),          f < F,
+ *   y_t(f)  = scale g(f, a) X_t(f),
+ *
+ * (a direct DFT; the Nyquist bin f = F is dropped).  raw is [N][S] int8, w is
+ * [P][2F] (NULL: all ones), g is [F][N] complex (NULL: 1).  out is [F][T][N]
+ * complex FP64 with T = floor((S - (P - 1) 2F) / 2F): the channel-major
+ * voltage layout the correlator reads.
+ */
+void oracle_fengine(const int8_t *raw, int64_t N, int64_t S, int F, int P, const double *w,
+                    const double *g, double scale, double *out)
+{
+    const int64_t M = 2 * (int64_t)F;
+    const int64_t T = S >= (P - 1) * M ? (S - (P - 1) * M) / M : 0;
+    const double two_pi = 6.283185307179586476925286766559;
+#pragma omp parallel for collapse(2) schedule(dynamic, 1)
+    for (int64_t a = 0; a < N; ++a)
+        for (int64_t t = 0; t < T; ++t) {
+            double *u = (double *)malloc(sizeof(double) * (size_t)M);
+            if (!u) continue;
+            for (int64_t n = 0; n < M; ++n) {
+                double acc = 0.0;
+                for (int p = 0; p < P; ++p)
+                    acc += (w ? w[p * M + n] : 1.0) * (double)raw[a * S + (t + p) * M + n];
+                u[n] = acc;
+            }
+            for (int64_t f = 0; f < F; ++f) {
+                double xr = 0.0, xi = 0.0;
+                for (int64_t n = 0; n < M; ++n) {
+                    const double ph = -two_pi * (double)((f * n) % M) / (double)M;
+                    xr += u[n] * cos(ph);
+                    xi += u[n] * sin(ph);
+                }
+                double gr = 1.0, gi = 0.0;
+                if (g) {
+                    gr = g[2 * (f * N + a)];
+                    gi = g[2 * (f * N + a) + 1];
+                }
+                double *o = out + 2 * ((f * T + t) * N + a);
+                o[0] = scale * (gr * xr - gi * xi);
+                o[1] = scale * (gr * xi + gi * xr);
+            }
+            free(u);
+        }
+}
+
+/* Quantiser of the F-engine output: round half to even, clip to [-127, 127]. */
+void oracle_quantize(const float *x, int64_t n, int8_t *q)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        double v = nearbyint((double)x[i]);   /* default rounding mode: half to even */
+        if (v > 127.0) v = 127.0;
+        if (v < -127.0) v = -127.0;
+        q[i] = (int8_t)v;
+    }
+}
+
 int oracle_max_dims(void) { return OR_MAX_DIMS; }
 
 /* Threads the OpenMP loops above use. */

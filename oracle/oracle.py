@@ -10,7 +10,8 @@ its redundancy counts (Sec. III), the geometry of Eq. GridEq, and the
 beam-space variant of Appendix A (steps 4-5: direct DFT of each level-1
 block into pointings, brute-force correlation over the coarser levels) and the
 tile hybrid of Sec. III (brute-force correlation of every ordered tile pair at
-every intra-tile offset).
+every intra-tile offset), and the F-engine of Appendix A step 2 (polyphase
+frames, direct DFT, gains, round-half-even int8 quantiser).
 """
 from __future__ import annotations
 
@@ -75,6 +76,12 @@ def lib() -> ctypes.CDLL:
         L.oracle_tile_correlate.restype = None
         L.oracle_tile_correlate.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int64,
                                             ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, f64p]
+        L.oracle_fengine.restype = None
+        L.oracle_fengine.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
+                                     ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
+                                     f64p]
+        L.oracle_quantize.restype = None
+        L.oracle_quantize.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
         L.oracle_max_dims.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -210,6 +217,35 @@ def tile_correlate(n1: int, n2: int, n_tiles: int, x) -> np.ndarray:
     lib().oracle_tile_correlate(n1, n2, n_tiles, C, T, code, a.ctypes.data_as(ctypes.c_void_p),
                                 _ptr(V, ctypes.c_double))
     return V[..., 0] + 1j * V[..., 1]
+
+
+def fengine(raw, F: int, P: int = 1, window=None, gains=None, scale: float = 1.0) -> np.ndarray:
+    """F-engine channel voltages (Appendix A step 2) as complex128 [F][T][N]:
+    polyphase sum of P frames of 2F samples, direct DFT, Nyquist bin dropped,
+    times scale and the per-(channel, antenna) complex gain."""
+    r = np.ascontiguousarray(np.asarray(raw.numpy() if hasattr(raw, "numpy") else raw, dtype=np.int8))
+    N, S = r.shape
+    M = 2 * F
+    T = (S - (P - 1) * M) // M if S >= (P - 1) * M else 0
+    w = None if window is None else np.ascontiguousarray(np.asarray(window, dtype=np.float64))
+    g = None
+    if gains is not None:
+        gc = np.asarray(gains, dtype=np.complex128).reshape(F, N)
+        g = np.ascontiguousarray(np.stack([gc.real, gc.imag], axis=-1))
+    out = np.zeros((F, T, N, 2))
+    lib().oracle_fengine(r.ctypes.data_as(ctypes.c_void_p), N, S, F, P,
+                         None if w is None else w.ctypes.data_as(ctypes.c_void_p),
+                         None if g is None else g.ctypes.data_as(ctypes.c_void_p), scale,
+                         _ptr(out, ctypes.c_double))
+    return out[..., 0] + 1j * out[..., 1]
+
+
+def quantize(x) -> np.ndarray:
+    """int8 codes of float32 values: round half to even, clip to [-127, 127]."""
+    a = np.ascontiguousarray(np.asarray(x, dtype=np.float32))
+    q = np.zeros(a.shape, dtype=np.int8)
+    lib().oracle_quantize(a.ctypes.data_as(ctypes.c_void_p), a.size, q.ctypes.data_as(ctypes.c_void_p))
+    return q
 
 
 # ---------------------------------------------------------------- physical baselines

@@ -455,3 +455,51 @@ def test_tile_numpy_cross_spectrum_route():
     idx = np.ix_(np.arange(-(n2 - 1), n2) % (2 * n2), np.arange(-(n1 - 1), n1) % (2 * n1))
     ref = g[..., idx[0], idx[1]].reshape(1, nt, nt, -1)
     assert relerr(oracle.tile_correlate(n1, n2, nt, x), ref) < 1e-12
+
+
+# ---------------------------------------------------------------- F-engine
+
+def test_fengine_single_tap_is_numpy_rfft_per_frame():
+    rng = np.random.default_rng(61)
+    N, F, T = 3, 8, 5
+    raw = rng.integers(-128, 128, size=(N, 2 * F * T)).astype(np.int8)
+    X = oracle.fengine(raw, F)
+    ref = np.fft.rfft(raw.reshape(N, T, 2 * F).astype(np.float64), axis=-1)[..., :F]
+    assert X.shape == (F, T, N)
+    assert relerr(X, ref.transpose(2, 1, 0)) < 1e-14
+
+
+def test_fengine_polyphase_frames_and_gains():
+    """P taps: the windowed sum of P consecutive frames, then the real FFT
+    (numpy, a different route); gains and scale multiply each channel."""
+    rng = np.random.default_rng(62)
+    N, F, P, S = 2, 16, 4, 2 * 16 * 9 + 5
+    raw = rng.integers(-100, 100, size=(N, S)).astype(np.int8)
+    w = rng.standard_normal(P * 2 * F)
+    g = rng.standard_normal((F, N)) + 1j * rng.standard_normal((F, N))
+    X = oracle.fengine(raw, F, P, window=w, gains=g, scale=0.25)
+    M = 2 * F
+    T = (S - (P - 1) * M) // M
+    frames = np.stack([raw[:, t * M:(t + P) * M].astype(np.float64) for t in range(T)], axis=1)
+    u = (frames.reshape(N, T, P, M) * w.reshape(P, M)).sum(axis=2)
+    ref = 0.25 * np.fft.rfft(u, axis=-1)[..., :F].transpose(2, 1, 0) * g[:, None, :]
+    assert X.shape == (F, T, N)
+    assert relerr(X, ref) < 1e-13
+
+
+def test_fengine_tone_closed_form():
+    """The period-4 sequence (A, 0, -A, 0) has all its power in channel F/2:
+    X(F/2) = A F, every other channel 0."""
+    N, F, T, A = 2, 32, 3, 100
+    pattern = np.array([A, 0, -A, 0], dtype=np.int8)
+    raw = np.tile(pattern, (N, 2 * F * T // 4))
+    X = oracle.fengine(raw, F)
+    expect = np.zeros((F, T, N), dtype=complex)
+    expect[F // 2] = A * F
+    np.testing.assert_allclose(X, expect, rtol=0, atol=1e-9)
+
+
+def test_quantizer_rounds_half_to_even_and_clips():
+    x = np.array([0.5, 1.5, 2.5, -0.5, -1.5, -2.5, 126.5, 127.49, 127.5, 300.0, -127.5, -1e9], dtype=np.float32)
+    np.testing.assert_array_equal(oracle.quantize(x),
+                                  np.array([0, 2, 2, 0, -2, -2, 126, 127, 127, 127, -127, -127], dtype=np.int8))
