@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-beams", action="store_true", help="skip the beam-space variant")
     ap.add_argument("--no-tiles", action="store_true", help="skip the tile-hybrid variant")
+    ap.add_argument("--no-fengine", action="store_true", help="skip the F-engine leg")
     return ap.parse_args()
 
 
@@ -188,6 +189,14 @@ def recorded_traffic(kernel_name, workload, precision, units_per_launch):
                     return b, "ncu, same launch size"
                 return b * units_per_launch / u, "ncu at %g channel-samples per launch, scaled" % u
     return None, None
+
+
+def hbm_peak_gbs():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return float(json.load(f).get("hbm_gbs", 6800.0))
+    return 6800.0
 
 
 def alu_peak_tflops(sm_mhz):
@@ -500,6 +509,41 @@ def run_ours(args):
         bp.close()
         del bvis
 
+    # F-engine (Appendix A step 2) producing this workload's voltages from raw
+    # int8 samples: F = the channel count, 4-tap polyphase frames, T frames
+    fe = None
+    if rank == 0 and not args.no_fengine:
+        F, P, T = w.channels, 4, w.samples
+        S = (T + P - 1) * 2 * F
+        gen = torch.Generator(device="cuda").manual_seed(9090007)
+        raw = torch.randint(-128, 128, (w.n_antennas, S), generator=gen, device="cuda",
+                            dtype=torch.int16).to(torch.int8)
+        n = torch.arange(P * 2 * F, dtype=torch.float64)
+        win = (torch.hann_window(P * 2 * F, periodic=False, dtype=torch.float64)
+               * torch.sinc((n - (P * 2 * F - 1) / 2) / (2 * F))).float().cuda()
+        fout = torch.empty((F, T, w.n_antennas, 2), dtype=torch.int8, device="cuda")
+        need = omni.load().omni_fengine_scratch_bytes(w.n_antennas, S, F, P)
+        fscr = torch.empty(need // 8, dtype=torch.float64, device="cuda")
+        for _ in range(3):
+            omni.fengine(raw, F, P, window=win, scale=0.05, out=fout, scratch=fscr)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 3
+        e0.record(stream)
+        for _ in range(reps):
+            omni.fengine(raw, F, P, window=win, scale=0.05, out=fout, scratch=fscr)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_f = e0.elapsed_time(e1) / reps
+        alg = raw.numel() + fout.numel()                  # raw in, int8 voltages out
+        design = alg + 2 * need                           # plus the FP32 spectra round trip
+        fe = {"value": w.n_antennas * T * F / (ms_f * 1e-3), "unit": UNIT, "ms_per_step": ms_f,
+              "channels": F, "taps": P, "frames": T, "antennas": w.n_antennas,
+              "hbm": {"algorithmic_bytes": alg, "design_bytes": design,
+                      "achieved_GBs_design": design / (ms_f * 1e-3) / 1e9,
+                      "frac_design": design / (ms_f * 1e-3) / 1e9 / hbm_peak_gbs()}}
+        del raw, fout, fscr
+
     # tile hybrid (Sec. III) on the same voltages: the level-1 blocks as tiles at
     # their level-2 positions, correlated pairwise by brute force; on this
     # lattice, summing tile pairs with equal grid offsets must give back the
@@ -560,7 +604,7 @@ def run_ours(args):
                 "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": sum(s["launches"] for s in stats),
                 "clocks": clocks, "epilogue": epilogue, "direct_n2": n2, "beam_space": beams,
-                "tile_hybrid": tiles,
+                "tile_hybrid": tiles, "fengine": fe,
                 "kernels": [{k: s[k] for k in ("name", "launches", "total_ms")}
                             for s in stats if s["launches"]]}
         if "fp32" in results and args.precision != "fp32":

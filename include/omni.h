@@ -135,6 +135,29 @@ omni_status omni_plan_create_beams(const omni_level* levels, int n_levels, int64
 omni_status omni_plan_create_tiles(const omni_level* tile, int64_t n_tiles, const double* offsets,
                                    int64_t n_channels, omni_dtype dtype, omni_plan** out);
 
+/* F-engine (Appendix A, step 2): channelise every antenna's real int8 sample
+ * stream into the correlator's input voltages.  Frame t of antenna a, with
+ * frame length 2F and P taps (polyphase filter bank):
+ *   u_t(n) = sum_{p<P} w[p 2F + n] r_a[(t + p) 2F + n],  n < 2F
+ *   X_t(f) = sum_{n<2F} u_t(n) exp(-2 pi i f n / 2F),    f < F (Nyquist dropped)
+ *   y_t(f) = scale g[f][a] X_t(f)
+ * raw_dev [n_antennas][n_samples] int8 (device); window_dev [P][2F] float or
+ * NULL (all ones); gains_dev [F][n_antennas] complex float (re, im) or NULL
+ * (1); out_dev [F][T][n_antennas] complex, OMNI_IN_CI8 (round half to even,
+ * clipped to +-127) or OMNI_IN_CF32, T = floor((n_samples - (P-1) 2F) / 2F)
+ * (returned in *n_frames): exactly what omni_correlate reads with C = F.
+ * scratch_dev: at least omni_fengine_scratch_bytes(...) bytes, 8-byte aligned,
+ * owned by the caller.  Asynchronous on stream; nothing is allocated.
+ * Errors: INVALID_ARG (NULL pointers, F not a power of two in [2, 4096], taps
+ * outside [1, 64], misaligned out/gains/scratch, scratch too small, a launch
+ * larger than 2^31 - 1 CTAs), CUDA. */
+int64_t omni_fengine_scratch_bytes(int64_t n_antennas, int64_t n_samples, int32_t n_channels,
+                                   int32_t taps);
+omni_status omni_fengine(const int8_t* raw_dev, int64_t n_antennas, int64_t n_samples,
+                         int32_t n_channels, int32_t taps, const float* window_dev,
+                         const float* gains_dev, float scale, omni_dtype out_dtype, void* out_dev,
+                         void* scratch_dev, int64_t scratch_bytes, int64_t* n_frames, void* stream);
+
 /* A plan for n_arrays independent arrays of possibly different hierarchies
  * (Sec. III: several separate omniscopes, each correlated on its own), all with
  * n_channels channels of the same dtype.  levels_per_array[a] has

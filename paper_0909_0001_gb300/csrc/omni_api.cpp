@@ -927,6 +927,44 @@ omni_status omni_plan_create_beams(const omni_level* levels, int n_levels, int64
     return create_plan(levels, n_levels, n_channels, dtype, OMNI_FP32, 1536, out, true);
 }
 
+int64_t omni_fengine_scratch_bytes(int64_t n_antennas, int64_t n_samples, int32_t n_channels,
+                                   int32_t taps) {
+    if (n_antennas < 1 || n_channels < 1 || taps < 1) return 0;
+    return (int64_t)sizeof(float2) * n_antennas * fengine_frames(n_samples, n_channels, taps) * n_channels;
+}
+
+omni_status omni_fengine(const int8_t* raw_dev, int64_t n_antennas, int64_t n_samples,
+                         int32_t n_channels, int32_t taps, const float* window_dev,
+                         const float* gains_dev, float scale, omni_dtype out_dtype, void* out_dev,
+                         void* scratch_dev, int64_t scratch_bytes, int64_t* n_frames, void* stream) {
+    const int64_t F = n_channels;
+    if (n_antennas < 1 || n_samples < 0) return fail(OMNI_ERR_INVALID_ARG, "need n_antennas >= 1, n_samples >= 0");
+    if (F < 2 || F > 4096 || !is_pow2(F))
+        return fail(OMNI_ERR_INVALID_ARG, "n_channels must be a power of two in [2, 4096], got %d", n_channels);
+    if (taps < 1 || taps > 64) return fail(OMNI_ERR_INVALID_ARG, "taps must be in [1, 64], got %d", taps);
+    if (out_dtype != OMNI_IN_CI8 && out_dtype != OMNI_IN_CF32)
+        return fail(OMNI_ERR_INVALID_ARG, "unknown output dtype %d", (int)out_dtype);
+    const int64_t T = fengine_frames(n_samples, n_channels, taps);
+    if (n_frames) *n_frames = T;
+    if (T == 0) return OMNI_OK;  // fewer samples than one frame: nothing to write
+    if (!raw_dev || !out_dev || !scratch_dev) return fail(OMNI_ERR_INVALID_ARG, "NULL raw, out or scratch");
+    if ((uintptr_t)out_dev % (out_dtype == OMNI_IN_CI8 ? 2 : 8) || (uintptr_t)scratch_dev % 8 ||
+        (gains_dev && (uintptr_t)gains_dev % 8) || (window_dev && (uintptr_t)window_dev % 4))
+        return fail(OMNI_ERR_INVALID_ARG, "misaligned out, scratch, gains or window pointer");
+    if (scratch_bytes < omni_fengine_scratch_bytes(n_antennas, n_samples, n_channels, taps))
+        return fail(OMNI_ERR_INVALID_ARG, "scratch holds %lld bytes, need %lld", (long long)scratch_bytes,
+                    (long long)omni_fengine_scratch_bytes(n_antennas, n_samples, n_channels, taps));
+    const int64_t ctas1 = n_antennas * ((T + 31) / 32), ctas2 = ((F + 31) / 32) * ((n_antennas + 31) / 32) * T;
+    if (ctas1 > INT32_MAX || ctas2 > INT32_MAX)
+        return fail(OMNI_ERR_INVALID_ARG, "launch too large: split the antennas or the samples");
+    cudaError_t e = launch_fengine(raw_dev, n_antennas, n_samples, n_channels, taps, window_dev,
+                                   reinterpret_cast<const float2*>(gains_dev), scale,
+                                   out_dtype == OMNI_IN_CI8, out_dev, reinterpret_cast<float2*>(scratch_dev),
+                                   (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "F-engine launch");
+    return OMNI_OK;
+}
+
 omni_status omni_plan_create_tiles(const omni_level* tile, int64_t n_tiles, const double* offsets,
                                    int64_t n_channels, omni_dtype dtype, omni_plan** out) {
     if (n_tiles < 1) return fail(OMNI_ERR_INVALID_ARG, "n_tiles must be >= 1");

@@ -98,6 +98,13 @@ cudaError_t upload_tc_tables();
 cudaError_t tc_occupancy(int kind, int* blocks_per_sm);
 int tc_stage_b_tile();  // level-1 frequencies per stage-B CTA
 
+// F-engine: frames per antenna, and the two launches (spectra into scratch
+// [N][T][F] float2, then calibrated, quantised or not, transposed to [F][T][N]).
+int64_t fengine_frames(int64_t n_samples, int32_t F, int32_t P);
+cudaError_t launch_fengine(const int8_t* raw, int64_t N, int64_t S, int32_t F, int32_t P,
+                           const float* window, const float2* gains, float scale, int out_i8,
+                           void* out, float2* scratch, cudaStream_t stream);
+
 // Tile hybrid: cross-spectrum accumulation between the tiles' padded spectra.
 cudaError_t launch_xspec(const Pass& p, const PassArgs& a, cudaStream_t stream);
 cudaError_t xspec_occupancy(int* blocks_per_sm);

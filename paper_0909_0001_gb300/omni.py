@@ -34,6 +34,7 @@ EXPORTS = (
     "omni_status_string", "omni_profile_enable", "omni_profile_read", "omni_correlate_noalloc",
     "omni_plan_create_batch", "omni_batch_info", "omni_radial_bins", "omni_unique_baselines",
     "omni_sum_groups", "omni_plan_create_beams", "omni_plan_create_tiles",
+    "omni_fengine_scratch_bytes", "omni_fengine",
 )
 
 
@@ -74,6 +75,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                                             P(vp)]),
         "omni_plan_create_beams": (ctypes.c_int, [lv, ctypes.c_int, i64, ctypes.c_int, P(vp)]),
         "omni_plan_create_tiles": (ctypes.c_int, [lv, i64, P(dbl), i64, ctypes.c_int, P(vp)]),
+        "omni_fengine_scratch_bytes": (i64, [i64, i64, i32, i32]),
+        "omni_fengine": (ctypes.c_int, [vp, i64, i64, i32, i32, vp, vp, ctypes.c_float, ctypes.c_int,
+                                        vp, vp, i64, P(i64), vp]),
         "omni_plan_destroy": (None, [vp]),
         "omni_plan_info": (ctypes.c_int, [vp, P(ctypes.c_int), P(i32), P(i32), P(i64), P(i64),
                                           P(i64)]),
@@ -202,6 +206,45 @@ def _stream_ptr(stream) -> ctypes.c_void_p:
     if stream is None:
         stream = torch.cuda.current_stream()
     return ctypes.c_void_p(int(stream.cuda_stream))
+
+
+def fengine(raw: torch.Tensor, channels: int, taps: int = 1, window: Optional[torch.Tensor] = None,
+            gains: Optional[torch.Tensor] = None, scale: float = 1.0, dtype: str = "ci8",
+            out: Optional[torch.Tensor] = None, scratch: Optional[torch.Tensor] = None,
+            stream=None) -> torch.Tensor:
+    """F-engine (Appendix A step 2): channelise raw int8 samples [N][S] (device)
+    into channel voltages [F][T][N][2] (int8 or float32), the layout Plan.correlate
+    reads with C = F.  window: [taps * 2F] float32 (None: ones); gains: [F][N]
+    complex64 (None: 1)."""
+    if raw.dtype != torch.int8 or raw.dim() != 2 or not raw.is_cuda or not raw.is_contiguous():
+        raise ValueError("raw must be a contiguous int8 CUDA tensor [N][S]")
+    N, S = raw.shape
+    L = load()
+    need = L.omni_fengine_scratch_bytes(N, S, channels, taps)
+    T = need // (8 * N * channels) if need else 0
+    if out is None:
+        out = torch.empty((channels, T, N, 2), dtype=torch.int8 if dtype == "ci8" else torch.float32,
+                          device=raw.device)
+    if scratch is None:
+        scratch = torch.empty(max(1, need // 8), dtype=torch.float64, device=raw.device)
+    wptr = None
+    if window is not None:
+        window = window.to(device=raw.device, dtype=torch.float32).contiguous()
+        if window.numel() != taps * 2 * channels:
+            raise ValueError("window must have taps * 2F values")
+        wptr = ctypes.c_void_p(window.data_ptr())
+    gptr = None
+    if gains is not None:
+        gains = torch.view_as_real(gains.to(device=raw.device, dtype=torch.complex64).contiguous())
+        if gains.numel() != 2 * channels * N:
+            raise ValueError("gains must be [F][N] complex")
+        gptr = ctypes.c_void_p(gains.data_ptr())
+    frames = ctypes.c_int64()
+    _check(L.omni_fengine(ctypes.c_void_p(raw.data_ptr()), N, S, channels, taps, wptr, gptr,
+                          float(scale), DTYPES[dtype], ctypes.c_void_p(out.data_ptr()),
+                          ctypes.c_void_p(scratch.data_ptr()), scratch.numel() * scratch.element_size(),
+                          ctypes.byref(frames), _stream_ptr(stream)))
+    return out
 
 
 class Plan:

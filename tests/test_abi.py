@@ -152,3 +152,16 @@ def test_tile_plans_check_geometry_without_a_gpu(lib):
     with pytest.raises(omni.OmniError) as e:
         omni.TilePlan(tile, np.zeros((0, 2)), 1)
     assert e.value.status == 1
+
+
+def test_fengine_argument_checks_without_a_gpu(lib):
+    f = lib.omni_fengine
+    # (n_antennas, n_samples, F, taps, out dtype) -> status; no pointer is touched
+    assert f(None, 4, 64, 3, 1, None, None, 1.0, 1, None, None, 0, None, None) == 1     # F not 2^k
+    assert f(None, 4, 64, 8192, 1, None, None, 1.0, 1, None, None, 0, None, None) == 1  # F too large
+    assert f(None, 4, 64, 8, 0, None, None, 1.0, 1, None, None, 0, None, None) == 1     # no taps
+    assert f(None, 4, 64, 8, 1, None, None, 1.0, 7, None, None, 0, None, None) == 1     # bad dtype
+    assert f(None, 4, 64, 32, 2, None, None, 1.0, 1, None, None, 0, None, None) == 0    # no frame
+    assert f(None, 4, 64, 8, 1, None, None, 1.0, 1, None, None, 0, None, None) == 1     # NULL buffers
+    assert lib.omni_fengine_scratch_bytes(4, 2 * 8 * 5 + 3, 8, 1) == 8 * 4 * 5 * 8
+    assert lib.omni_fengine_scratch_bytes(4, 100, 64, 2) == 0
