@@ -101,6 +101,26 @@ omni_status omni_baselines(const omni_level* levels, int n_levels, int32_t* dm,
 omni_status omni_plan_create(const omni_level* levels, int n_levels, int64_t n_channels,
                              omni_dtype dtype, omni_precision precision, omni_plan** out);
 
+/* Autotuned plan: times candidate plans for this problem on the caller's
+ * voltages volts_dev ([C][T][N], as omni_correlate takes them) and returns the
+ * fastest.  Candidates: chunk buffer size (384, 768, 1536, 3072 MB) x overlap of
+ * consecutive chunks' passes x, for the FP32 path, level passes (both axes of
+ * a square level in one kernel) or one pass per axis, or, for the mixed path,
+ * the share of each chunk's last pass on tensor cores (all, 0.3, 0.6) with the
+ * rest on the FP32 level kernel.  Each candidate runs one warm-up and two
+ * timed omni_correlate calls on a private stream (their accumulators are
+ * discarded).  cache_path (or NULL): a text file of one JSON object per line,
+ * keyed by level shapes, precision, dtype, C, T and device name; a hit skips
+ * the search (*from_cache = 1), a search appends its winner.  Errors: as
+ * omni_plan_create; INVALID_ARG for NULL volts_dev or T < 1. */
+omni_status omni_plan_create_tuned(const omni_level* levels, int n_levels, int64_t n_channels,
+                                   omni_dtype dtype, omni_precision precision, const void* volts_dev,
+                                   int64_t T, const char* cache_path, int* from_cache, omni_plan** out);
+
+/* The choices a plan was built with (any output may be NULL). */
+omni_status omni_plan_knobs(const omni_plan* plan, int64_t* chunk_mb, int* overlap, int* level_passes,
+                            double* split_tc);
+
 /* Beam-space plan (Appendix A, steps 4-5): each level-1 block is Fourier
  * transformed unpadded, giving n1 x n2 digital pointings k = (k_a, k_b), and
  * the correlation runs over the axes of levels 2..n only:

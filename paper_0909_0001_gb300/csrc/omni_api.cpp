@@ -203,15 +203,35 @@ void omni::set_last_error(const char* msg) { g_last_error = msg; }
 
 // ----------------------------------------------------------------------------- plan
 
+// Tunable choices of a plan (the autotuner searches these; environment
+// variables override the defaults for experiments).
+struct Knobs {
+    int64_t chunk_mb = 1536;      // target size of each chunk scratch buffer (OMNI_CHUNK_MB)
+    int64_t chunk_channels = 0;   // channels per chunk, 0 = one wave of the last pass (OMNI_CHUNK_CHANNELS)
+    int overlap = 1;              // overlap the two passes of consecutive chunks (OMNI_OVERLAP)
+    int level_passes = 1;         // both axes of a square level in one pass (OMNI_LEVEL_PASSES)
+    double split_tc = 0.0;        // mixed: share of a chunk's channels on tensor cores, 0 = all (OMNI_SPLIT_TC)
+};
+
+Knobs knobs_from_env() {
+    Knobs k;
+    if (const char* e = std::getenv("OMNI_CHUNK_MB")) k.chunk_mb = std::max<int64_t>(1, std::atoll(e));
+    if (const char* e = std::getenv("OMNI_CHUNK_CHANNELS")) k.chunk_channels = std::max<int64_t>(0, std::atoll(e));
+    if (const char* e = std::getenv("OMNI_OVERLAP")) k.overlap = std::atoi(e) != 0;
+    if (const char* e = std::getenv("OMNI_LEVEL_PASSES")) k.level_passes = std::atoi(e) != 0;
+    if (const char* e = std::getenv("OMNI_SPLIT_TC")) k.split_tc = std::atof(e);
+    return k;
+}
+
 struct omni_plan {
     int device = 0;
+    Knobs knobs;
     Geometry g;
     int64_t C = 0;
     omni_dtype dtype = OMNI_IN_CF32;
     omni_precision precision = OMNI_FP32;
     std::vector<Pass> fwd, inv;
     int64_t Cc = 1, Tc = 1;   // forward chunk: channels x samples
-    int64_t chunk_mb = 1536;  // target size of each chunk scratch buffer
     bool beams = false;       // beam-space plan: level-1 axes unpadded, no lag over them
     int64_t n_tiles = 0;      // tile-hybrid plan: identical tiles at arbitrary offsets
     double inv_scale = 1.0;   // 1 / (points of the inverse transform)
@@ -328,9 +348,8 @@ omni_status build_passes(omni_plan* pl) {
     // forward: increasing axis order; inputs [outer n_e>d][n_d][inner L_e<d].
     // A level whose two axes have the same power-of-two padded length <= 64 is
     // transformed by one level pass (both axes in shared memory); other axes
-    // get one pass each.  OMNI_LEVEL_PASSES=0 forces one pass per axis.
-    bool use_level = true;
-    if (const char* env = std::getenv("OMNI_LEVEL_PASSES")) use_level = std::atoi(env) != 0;
+    // get one pass each (knob level_passes = 0 forces one pass per axis).
+    const bool use_level = pl->knobs.level_passes != 0;
     std::vector<std::pair<int, bool>> stages;  // (first axis, is a level pass)
     for (size_t a = 0; a < axes.size(); ++a) {
         const int d = axes[a];
@@ -466,8 +485,7 @@ omni_status build_passes(omni_plan* pl) {
 // 2-level workload, FP32 path: 96 MB 33.7 ms, 192 MB 26.6, 384 MB 22.6,
 // 768 MB 21.3, 1536 MB 20.8 ms per step).
 void choose_chunks(omni_plan* pl) {
-    int64_t mb = pl->chunk_mb;
-    if (const char* env = std::getenv("OMNI_CHUNK_MB")) mb = std::max<int64_t>(1, std::atoll(env));
+    const int64_t mb = pl->knobs.chunk_mb;
     const int64_t target = mb << 20;
     // CTAs the last pass runs per channel of a chunk
     const Pass& last = pl->fwd.back();
@@ -494,8 +512,7 @@ void choose_chunks(omni_plan* pl) {
     if (sms <= 0) slots = 304;
     // fill one wave of the last pass: as many channels as the slots hold
     pl->Cc = std::min<int64_t>(pl->C, std::max<int64_t>(1, slots / ctas));
-    if (const char* env = std::getenv("OMNI_CHUNK_CHANNELS"))
-        pl->Cc = std::min<int64_t>(pl->C, std::max<int64_t>(1, std::atoll(env)));
+    if (pl->knobs.chunk_channels > 0) pl->Cc = std::min<int64_t>(pl->C, pl->knobs.chunk_channels);
     const int64_t per_sample = std::max<int64_t>(1, pl->fwd_elems) * (int64_t)sizeof(float2);
     const int64_t samples = std::max<int64_t>(1, target / per_sample);
     pl->Tc = std::max<int64_t>(1, std::min<int64_t>(1024, samples / pl->Cc));
@@ -913,18 +930,185 @@ omni_status omni_unique_baselines(const omni_level* levels, int n_levels, int64_
 }
 
 static omni_status create_plan(const omni_level* levels, int n_levels, int64_t n_channels,
-                               omni_dtype dtype, omni_precision precision, int64_t chunk_mb,
+                               omni_dtype dtype, omni_precision precision, const Knobs& knobs,
                                omni_plan** out, bool beams = false, int64_t n_tiles = 0,
                                const double* tile_offsets = nullptr);
 
 omni_status omni_plan_create(const omni_level* levels, int n_levels, int64_t n_channels,
                              omni_dtype dtype, omni_precision precision, omni_plan** out) {
-    return create_plan(levels, n_levels, n_channels, dtype, precision, 1536, out);
+    return create_plan(levels, n_levels, n_channels, dtype, precision, knobs_from_env(), out);
 }
 
 omni_status omni_plan_create_beams(const omni_level* levels, int n_levels, int64_t n_channels,
                                    omni_dtype dtype, omni_plan** out) {
-    return create_plan(levels, n_levels, n_channels, dtype, OMNI_FP32, 1536, out, true);
+    return create_plan(levels, n_levels, n_channels, dtype, OMNI_FP32, knobs_from_env(), out, true);
+}
+
+// ---------------------------------------------------------------- autotuner
+
+}  // extern "C"
+
+namespace {
+
+// Cache key: the problem (level shapes, precision, input type, channels,
+// samples per call) and the device.
+std::string tune_key(const Geometry& g, omni_precision precision, omni_dtype dtype, int64_t C,
+                     int64_t T, int device) {
+    cudaDeviceProp prop{};
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) prop.name[0] = 0;
+    std::string k;
+    for (int d = 0; d < g.D; ++d) k += std::to_string(g.n[d]) + (d + 1 < g.D ? "x" : "");
+    k += "|p" + std::to_string((int)precision) + "|d" + std::to_string((int)dtype) + "|C" +
+         std::to_string(C) + "|T" + std::to_string(T) + "|" + prop.name + "|v1";
+    for (char& c : k)
+        if (c == '"' || c == '\\' || c == '\n') c = '_';
+    return k;
+}
+
+// One cache entry per line: {"key": "...", "chunk_mb": M, "chunk_channels": K,
+// "overlap": O, "level_passes": L, "split_tc": S, "ms": X}
+bool tune_cache_read(const char* path, const std::string& key, Knobs& k) {
+    if (!path) return false;
+    FILE* f = std::fopen(path, "r");
+    if (!f) return false;
+    char line[1024];
+    bool found = false;
+    const std::string want = "\"key\": \"" + key + "\"";
+    while (std::fgets(line, sizeof line, f)) {
+        if (!std::strstr(line, want.c_str())) continue;
+        Knobs t;
+        long long mb = 0, ch = 0;
+        int ov = 0, lp = 0;
+        double sp = 0.0;
+        const char* q = std::strstr(line, "\"chunk_mb\":");
+        if (!q || std::sscanf(q, "\"chunk_mb\": %lld, \"chunk_channels\": %lld, \"overlap\": %d, "
+                                 "\"level_passes\": %d, \"split_tc\": %lf", &mb, &ch, &ov, &lp, &sp) != 5)
+            continue;
+        t.chunk_mb = std::max<long long>(1, mb);
+        t.chunk_channels = std::max<long long>(0, ch);
+        t.overlap = ov != 0;
+        t.level_passes = lp != 0;
+        t.split_tc = sp;
+        k = t;
+        found = true;  // the last matching line wins
+    }
+    std::fclose(f);
+    return found;
+}
+
+void tune_cache_write(const char* path, const std::string& key, const Knobs& k, double ms) {
+    if (!path) return;
+    FILE* f = std::fopen(path, "a");
+    if (!f) return;
+    std::fprintf(f, "{\"key\": \"%s\", \"chunk_mb\": %lld, \"chunk_channels\": %lld, \"overlap\": %d, "
+                    "\"level_passes\": %d, \"split_tc\": %.3f, \"ms\": %.4f}\n",
+                 key.c_str(), (long long)k.chunk_mb, (long long)k.chunk_channels, k.overlap, k.level_passes,
+                 k.split_tc, ms);
+    std::fclose(f);
+}
+
+}  // namespace
+
+extern "C" {
+
+omni_status omni_plan_create_tuned(const omni_level* levels, int n_levels, int64_t n_channels,
+                                   omni_dtype dtype, omni_precision precision, const void* volts_dev,
+                                   int64_t T, const char* cache_path, int* from_cache, omni_plan** out) {
+    if (!out) return fail(OMNI_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (from_cache) *from_cache = 0;
+    if (!volts_dev || T < 1) return fail(OMNI_ERR_INVALID_ARG, "the tuner needs device voltages and T >= 1");
+    Geometry g;
+    omni_status st = make_geometry(levels, n_levels, g);
+    if (st != OMNI_OK) return st;
+    int device = 0;
+    if (cudaGetDevice(&device) != cudaSuccess) return fail(OMNI_ERR_CUDA, "cudaGetDevice failed");
+    const std::string key = tune_key(g, precision, dtype, n_channels, T, device);
+    Knobs best;
+    if (tune_cache_read(cache_path, key, best)) {
+        if (from_cache) *from_cache = 1;
+        return create_plan(levels, n_levels, n_channels, dtype, precision, best, out);
+    }
+    // candidates: chunk size x chunk overlap x level passes (FP32) or the
+    // tensor-core / FP32 split of the last pass (mixed)
+    std::vector<Knobs> cands;
+    for (int64_t mb : {384, 768, 1536, 3072})
+        for (int ov : {1, 0}) {
+            if (precision == OMNI_MIXED_FP16) {
+                for (double sp : {0.0, 0.3, 0.6}) {
+                    Knobs k;
+                    k.chunk_mb = mb;
+                    k.overlap = ov;
+                    k.split_tc = sp;
+                    if (sp > 0.0 && !ov) continue;  // the split needs the overlapped schedule
+                    cands.push_back(k);
+                }
+            } else {
+                for (int lp : {1, 0}) {
+                    Knobs k;
+                    k.chunk_mb = mb;
+                    k.overlap = ov;
+                    k.level_passes = lp;
+                    cands.push_back(k);
+                }
+            }
+        }
+    cudaStream_t stream = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (stream) cudaStreamDestroy(stream);
+        if (e0) cudaEventDestroy(e0);
+        return fail(OMNI_ERR_CUDA, "tuner stream/events");
+    }
+    double best_ms = -1.0;
+    omni_status last_err = OMNI_OK;
+    for (const Knobs& k : cands) {
+        omni_plan* pl = nullptr;
+        st = create_plan(levels, n_levels, n_channels, dtype, precision, k, &pl);
+        if (st != OMNI_OK) {  // e.g. a chunk size that does not fit: skip it
+            last_err = st;
+            cudaGetLastError();
+            continue;
+        }
+        float ms = 0.f;
+        st = omni_correlate(pl, volts_dev, T, stream);  // warm-up
+        if (st == OMNI_OK) {
+            cudaEventRecord(e0, stream);
+            for (int r = 0; r < 2 && st == OMNI_OK; ++r) st = omni_correlate(pl, volts_dev, T, stream);
+            cudaEventRecord(e1, stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+                st = OMNI_ERR_CUDA;
+        }
+        if (st == OMNI_OK) st = check_device_error(pl);
+        omni_plan_destroy(pl);
+        if (st != OMNI_OK) {
+            last_err = st;
+            continue;
+        }
+        if (best_ms < 0.0 || ms / 2.0 < best_ms) {
+            best_ms = ms / 2.0;
+            best = k;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamDestroy(stream);
+    if (best_ms < 0.0)
+        return last_err != OMNI_OK ? last_err : fail(OMNI_ERR_UNSUPPORTED, "no tuner candidate ran");
+    tune_cache_write(cache_path, key, best, best_ms);
+    return create_plan(levels, n_levels, n_channels, dtype, precision, best, out);
+}
+
+omni_status omni_plan_knobs(const omni_plan* pl, int64_t* chunk_mb, int* overlap, int* level_passes,
+                            double* split_tc) {
+    if (!pl) return fail(OMNI_ERR_INVALID_ARG, "plan is NULL");
+    const omni_plan* q = pl->members.empty() ? pl : pl->members.front();
+    if (chunk_mb) *chunk_mb = q->knobs.chunk_mb;
+    if (overlap) *overlap = q->overlap ? 1 : 0;
+    if (level_passes) *level_passes = q->knobs.level_passes;
+    if (split_tc) *split_tc = q->split ? q->split_tc : 0.0;
+    return OMNI_OK;
 }
 
 int64_t omni_fengine_scratch_bytes(int64_t n_antennas, int64_t n_samples, int32_t n_channels,
@@ -970,11 +1154,11 @@ omni_status omni_plan_create_tiles(const omni_level* tile, int64_t n_tiles, cons
     if (n_tiles < 1) return fail(OMNI_ERR_INVALID_ARG, "n_tiles must be >= 1");
     if (!offsets) return fail(OMNI_ERR_INVALID_ARG, "offsets is NULL");
     if (n_tiles > 4096) return fail(OMNI_ERR_UNSUPPORTED, "at most 4096 tiles");
-    return create_plan(tile, 1, n_channels, dtype, OMNI_FP32, 1536, out, false, n_tiles, offsets);
+    return create_plan(tile, 1, n_channels, dtype, OMNI_FP32, knobs_from_env(), out, false, n_tiles, offsets);
 }
 
 static omni_status create_plan(const omni_level* levels, int n_levels, int64_t n_channels,
-                               omni_dtype dtype, omni_precision precision, int64_t chunk_mb,
+                               omni_dtype dtype, omni_precision precision, const Knobs& knobs,
                                omni_plan** out, bool beams, int64_t n_tiles,
                                const double* tile_offsets) {
     if (!out) return fail(OMNI_ERR_INVALID_ARG, "out is NULL");
@@ -992,6 +1176,7 @@ static omni_status create_plan(const omni_level* levels, int n_levels, int64_t n
     omni_plan* pl = new omni_plan();
     pl->beams = beams;
     pl->n_tiles = n_tiles;
+    pl->knobs = knobs;
     omni_status st = make_geometry(levels, n_levels, pl->g, beams);
     if (st == OMNI_OK) st = n_tiles ? tile_geometry(pl->g, n_tiles, tile_offsets) : check_unique(pl->g);
     if (st != OMNI_OK) {
@@ -1023,11 +1208,9 @@ static omni_status create_plan(const omni_level* levels, int n_levels, int64_t n
         release(pl);
         return st;
     }
-    pl->chunk_mb = chunk_mb;
     choose_chunks(pl);
     // overlap the two passes of consecutive chunks (OMNI_OVERLAP=0 turns it off)
-    pl->overlap = pl->fwd.size() == 2;
-    if (const char* env = std::getenv("OMNI_OVERLAP")) pl->overlap = pl->overlap && std::atoi(env) != 0;
+    pl->overlap = pl->fwd.size() == 2 && pl->knobs.overlap != 0;
     if (pl->overlap) {
         if ((e = cudaStreamCreateWithFlags(&pl->aux_stream, cudaStreamNonBlocking)) != cudaSuccess ||
             (e = cudaEventCreateWithFlags(&pl->start_ev, cudaEventDisableTiming)) != cudaSuccess) {
@@ -1046,8 +1229,7 @@ static omni_status create_plan(const omni_level* levels, int n_levels, int64_t n
         // fraction of a chunk's channels on tensor cores (off by default: with
         // 768 MB chunks on the 2-level workload, no split 22.56 ms, 0.6 22.47,
         // 0.3 24.07 ms per step -- both kernels are issue-limited)
-        double frac = 0.0;
-        if (const char* env = std::getenv("OMNI_SPLIT_TC")) frac = std::atof(env);
+        const double frac = pl->knobs.split_tc;
         if (frac < 1.0 && frac > 0.0) {
             const Pass& last = pl->fwd.back();
             Pass sp{};
@@ -1142,7 +1324,7 @@ omni_status omni_plan_create_batch(const omni_level* const* levels_per_array,
         while (b < n_arrays && same_shape(a, b)) ++b;
         omni_plan* sub = nullptr;
         omni_status st = create_plan(levels_per_array[a], n_levels_per_array[a],
-                                     (int64_t)(b - a) * n_channels, dtype, precision, 1536, &sub);
+                                     (int64_t)(b - a) * n_channels, dtype, precision, knobs_from_env(), &sub);
         if (st != OMNI_OK) {
             release(pl);
             return st;

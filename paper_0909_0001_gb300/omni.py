@@ -34,7 +34,7 @@ EXPORTS = (
     "omni_status_string", "omni_profile_enable", "omni_profile_read", "omni_correlate_noalloc",
     "omni_plan_create_batch", "omni_batch_info", "omni_radial_bins", "omni_unique_baselines",
     "omni_sum_groups", "omni_plan_create_beams", "omni_plan_create_tiles",
-    "omni_fengine_scratch_bytes", "omni_fengine",
+    "omni_fengine_scratch_bytes", "omni_fengine", "omni_plan_create_tuned", "omni_plan_knobs",
 )
 
 
@@ -76,6 +76,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "omni_plan_create_beams": (ctypes.c_int, [lv, ctypes.c_int, i64, ctypes.c_int, P(vp)]),
         "omni_plan_create_tiles": (ctypes.c_int, [lv, i64, P(dbl), i64, ctypes.c_int, P(vp)]),
         "omni_fengine_scratch_bytes": (i64, [i64, i64, i32, i32]),
+        "omni_plan_create_tuned": (ctypes.c_int, [lv, ctypes.c_int, i64, ctypes.c_int, ctypes.c_int, vp,
+                                                  i64, ctypes.c_char_p, P(ctypes.c_int), P(vp)]),
+        "omni_plan_knobs": (ctypes.c_int, [vp, P(i64), P(ctypes.c_int), P(ctypes.c_int), P(dbl)]),
         "omni_fengine": (ctypes.c_int, [vp, i64, i64, i32, i32, vp, vp, ctypes.c_float, ctypes.c_int,
                                         vp, vp, i64, P(i64), vp]),
         "omni_plan_destroy": (None, [vp]),
@@ -271,10 +274,44 @@ class Plan:
 
     def _create(self) -> ctypes.c_void_p:
         h = ctypes.c_void_p()
+        tune = getattr(self, "_tune", None)
+        if tune is not None:
+            volts, cache = tune
+            T = self._check_volts_shape(volts)
+            hit = ctypes.c_int()
+            _check(load().omni_plan_create_tuned(
+                _levels(self.levels), len(self.levels), self.channels, DTYPES[self.dtype],
+                PRECISIONS[self.precision], ctypes.c_void_p(volts.data_ptr()), T,
+                None if cache is None else os.fsencode(cache), ctypes.byref(hit), ctypes.byref(h)))
+            self.from_cache = bool(hit.value)
+            return h
         _check(load().omni_plan_create(_levels(self.levels), len(self.levels), self.channels,
                                        DTYPES[self.dtype], PRECISIONS[self.precision],
                                        ctypes.byref(h)))
         return h
+
+    @classmethod
+    def tuned(cls, levels: Sequence[Level], channels: int, volts: torch.Tensor, dtype: str = "cf32",
+              precision: str = "fp32", cache: Optional[str] = None) -> "Plan":
+        """A plan whose chunking, overlap and pass structure were chosen by timing
+        candidates on these device voltages [C][T][N][2] (cached in `cache`)."""
+        self = cls.__new__(cls)
+        self._tune = (volts, cache)
+        cls.__init__(self, levels, channels, dtype=dtype, precision=precision)
+        self._tune = None
+        return self
+
+    def knobs(self) -> dict:
+        mb, ov, lp, sp = ctypes.c_int64(), ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        _check(load().omni_plan_knobs(self._h, ctypes.byref(mb), ctypes.byref(ov), ctypes.byref(lp),
+                                      ctypes.byref(sp)))
+        return {"chunk_mb": mb.value, "overlap": bool(ov.value), "level_passes": bool(lp.value),
+                "split_tc": sp.value}
+
+    def _check_volts_shape(self, v: torch.Tensor) -> int:
+        if not v.is_cuda or not v.is_contiguous() or v.dim() != 4 or v.shape[0] != self.channels:
+            raise ValueError("tuning voltages must be contiguous CUDA [C][T][N][2]")
+        return int(v.shape[1])
 
     # ---------------------------------------------------------------- checks
     def _check_volts(self, v: torch.Tensor) -> int:
