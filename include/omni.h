@@ -167,7 +167,9 @@ omni_status omni_plan_create_tiles(const omni_level* tile, int64_t n_tiles, cons
  * clipped to +-127) or OMNI_IN_CF32, T = floor((n_samples - (P-1) 2F) / 2F)
  * (returned in *n_frames): exactly what omni_correlate reads with C = F.
  * scratch_dev: at least omni_fengine_scratch_bytes(...) bytes, 8-byte aligned,
- * owned by the caller.  Asynchronous on stream; nothing is allocated.
+ * owned by the caller (0 bytes, and scratch_dev may be NULL, when F <= 256: one
+ * fused pass; larger F stage the spectra [N][T][F] FP32 there).  Asynchronous
+ * on stream; nothing is allocated.
  * Errors: INVALID_ARG (NULL pointers, F not a power of two in [2, 4096], taps
  * outside [1, 64], misaligned out/gains/scratch, scratch too small, a launch
  * larger than 2^31 - 1 CTAs), CUDA. */

@@ -1114,7 +1114,7 @@ omni_status omni_plan_knobs(const omni_plan* pl, int64_t* chunk_mb, int* overlap
 int64_t omni_fengine_scratch_bytes(int64_t n_antennas, int64_t n_samples, int32_t n_channels,
                                    int32_t taps) {
     if (n_antennas < 1 || n_channels < 1 || taps < 1) return 0;
-    return (int64_t)sizeof(float2) * n_antennas * fengine_frames(n_samples, n_channels, taps) * n_channels;
+    return fengine_scratch_bytes(n_antennas, n_samples, n_channels, taps);
 }
 
 omni_status omni_fengine(const int8_t* raw_dev, int64_t n_antennas, int64_t n_samples,
@@ -1131,15 +1131,16 @@ omni_status omni_fengine(const int8_t* raw_dev, int64_t n_antennas, int64_t n_sa
     const int64_t T = fengine_frames(n_samples, n_channels, taps);
     if (n_frames) *n_frames = T;
     if (T == 0) return OMNI_OK;  // fewer samples than one frame: nothing to write
-    if (!raw_dev || !out_dev || !scratch_dev) return fail(OMNI_ERR_INVALID_ARG, "NULL raw, out or scratch");
+    const int64_t need = omni_fengine_scratch_bytes(n_antennas, n_samples, n_channels, taps);
+    if (!raw_dev || !out_dev || (need > 0 && !scratch_dev))
+        return fail(OMNI_ERR_INVALID_ARG, "NULL raw, out or scratch");
     if ((uintptr_t)out_dev % (out_dtype == OMNI_IN_CI8 ? 2 : 8) || (uintptr_t)scratch_dev % 8 ||
         (gains_dev && (uintptr_t)gains_dev % 8) || (window_dev && (uintptr_t)window_dev % 4))
         return fail(OMNI_ERR_INVALID_ARG, "misaligned out, scratch, gains or window pointer");
-    if (scratch_bytes < omni_fengine_scratch_bytes(n_antennas, n_samples, n_channels, taps))
+    if (scratch_bytes < need)
         return fail(OMNI_ERR_INVALID_ARG, "scratch holds %lld bytes, need %lld", (long long)scratch_bytes,
-                    (long long)omni_fengine_scratch_bytes(n_antennas, n_samples, n_channels, taps));
-    const int64_t ctas1 = n_antennas * ((T + 31) / 32), ctas2 = ((F + 31) / 32) * ((n_antennas + 31) / 32) * T;
-    if (ctas1 > INT32_MAX || ctas2 > INT32_MAX)
+                    (long long)need);
+    if (fengine_ctas(n_antennas, T, n_channels) > INT32_MAX)
         return fail(OMNI_ERR_INVALID_ARG, "launch too large: split the antennas or the samples");
     cudaError_t e = launch_fengine(raw_dev, n_antennas, n_samples, n_channels, taps, window_dev,
                                    reinterpret_cast<const float2*>(gains_dev), scale,

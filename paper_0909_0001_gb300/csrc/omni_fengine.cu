@@ -6,15 +6,20 @@
 //   u_t(n) = sum_p w(p 2F + n) r_a((t + p) 2F + n)         (polyphase sum)
 //   X_t(f) = sum_n u_t(n) exp(-2 pi i f n / 2F), f < F     (real FFT, Nyquist dropped)
 //   y_t(f) = scale g(f, a) X_t(f)                          (calibration)
-// Kernel 1 packs the real frame as F complex points z(m) = u(2m) + i u(2m+1),
-// runs an F-point radix-2 FFT in shared memory and unpacks the real spectrum;
-// kernel 2 applies gains and scale, quantises (round half to even, clip to
-// +-127) or keeps FP32, and transposes [N][T][F] -> [F][T][N] through
+// The real frame is packed as F complex points z(m) = u(2m) + i u(2m+1), run
+// through an F-point radix-2 FFT in shared memory and unpacked to the real
+// spectrum.  F <= 256: one fused pass per 16 antennas, outputs written as
+// 16-antenna rows.  Larger F: kernel 1 writes the spectra [N][T][F] to a
+// scratch buffer, kernel 2 applies gains and scale, quantises (round half to
+// even, clip to +-127) or keeps FP32, and transposes to [F][T][N] through
 // shared-memory tiles so that both sides are coalesced.
 #include "omni_fft_common.cuh"
 #include "omni.h"
 
 #include <algorithm>
+#include <cmath>
+#include <mutex>
+#include <vector>
 
 namespace omni {
 namespace {
@@ -127,11 +132,159 @@ __global__ void __launch_bounds__(256) fengine_out(const float2* __restrict__ in
     }
 }
 
+// e^{-2 pi i j / 8192}, j < 4096, built on the host in double: every twiddle of
+// an F-point stage (e^{-i pi pos / half} = entry pos * 4096 / half) and of the
+// real-spectrum unpacking (e^{-i pi f / F} = entry f * 4096 / F) for F <= 4096.
+__device__ float2 g_fetw[4096];
+
+constexpr int kFuseAnt = 16;     // antennas per CTA: 32-byte int8 output rows
+constexpr int kFusePoints = 4096;  // complex points in shared memory (32 KB)
+static_assert(kFuseAnt == 16 && kFusePoints / kFuseAnt == 256, "fused index shifts assume 16 x 256 points");
+
+// Fused F-engine for F <= 256: CTA = (16 consecutive antennas, FR frames),
+// FR = 256 / F; polyphase, FFT, unpacking, calibration and quantisation in
+// shared memory, each output row (channel f, frame t) written as the 16
+// antennas' values together, so no intermediate spectrum goes through HBM.
+template <bool I8, bool VEC>
+__global__ void __launch_bounds__(kFThreads) fengine_fused(const int8_t* __restrict__ raw, int64_t N,
+                                                           int64_t S, int F, int logF, int P,
+                                                           const float* __restrict__ w, int64_t T,
+                                                           const float2* __restrict__ gains, float scale,
+                                                           void* __restrict__ out) {
+    // [antenna][frame][F]: each antenna's 256 points padded to 257 so that the
+    // 16 antennas of an output row fall in different banks
+    constexpr int kPad = kFusePoints / kFuseAnt + 1;
+    __shared__ float2 z[kFuseAnt * kPad];
+    // per antenna: FR frames x F points = 256 points; all index splits below
+    // are shifts and masks (F is a power of two)
+    constexpr int per = kFusePoints / kFuseAnt, logPer = 8, n = kFusePoints;
+    const int FR = per >> logF;
+    const int64_t tchunks = (T + FR - 1) / FR;
+    const int64_t a0 = (blockIdx.x / tchunks) * kFuseAnt;
+    const int64_t t0 = (blockIdx.x % tchunks) * FR;
+    const int64_t M = 2 * (int64_t)F;
+    const int tw_shift = 12 - logF;  // 4096 / F = 2^(12 - logF)
+    // polyphase sums, packed (even, odd), bit-reversed within each frame.
+    // VEC (rows 16-byte aligned, F >= 8): a thread takes 8 packed points, one
+    // 16-byte load of samples and four of window weights per tap
+    if (VEC) {
+        for (int idx = threadIdx.x; idx < n / 8; idx += kFThreads) {
+            const int al = idx >> (logPer - 3), rem = idx & (per / 8 - 1), fr = rem >> (logF - 3);
+            const int m0 = 8 * (rem & ((F >> 3) - 1));
+            const int64_t a = a0 + al, t = t0 + fr;
+            float ue[8], uo[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) ue[k] = uo[k] = 0.f;
+            if (a < N && t < T) {
+                const int8_t* ra = raw + a * S;
+                for (int p = 0; p < P; ++p) {
+                    const int4 rv = __ldg(reinterpret_cast<const int4*>(ra + (t + p) * M + 2 * m0));
+                    const int8_t* r = reinterpret_cast<const int8_t*>(&rv);
+                    float wv[16];
+                    if (w) {
+                        const float4* w4 = reinterpret_cast<const float4*>(w + p * M + 2 * m0);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const float4 x = __ldg(w4 + q);
+                            wv[4 * q] = x.x;
+                            wv[4 * q + 1] = x.y;
+                            wv[4 * q + 2] = x.z;
+                            wv[4 * q + 3] = x.w;
+                        }
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) wv[q] = 1.f;
+                    }
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        ue[k] = fmaf(wv[2 * k], (float)r[2 * k], ue[k]);
+                        uo[k] = fmaf(wv[2 * k + 1], (float)r[2 * k + 1], uo[k]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                z[al * kPad + fr * F + (int)(__brev((unsigned)(m0 + k)) >> (32 - logF))] = make_float2(ue[k], uo[k]);
+        }
+    } else
+    for (int idx = threadIdx.x; idx < n; idx += kFThreads) {
+        const int al = idx >> logPer, rem = idx & (per - 1), fr = rem >> logF, m = rem & (F - 1);
+        const int64_t a = a0 + al, t = t0 + fr;
+        float ue = 0.f, uo = 0.f;
+        if (a < N && t < T) {
+            const int8_t* ra = raw + a * S;
+            for (int p = 0; p < P; ++p) {
+                const int8_t* r = ra + (t + p) * M + 2 * m;
+                const float we = w ? __ldg(w + p * M + 2 * m) : 1.f;
+                const float wo = w ? __ldg(w + p * M + 2 * m + 1) : 1.f;
+                ue = fmaf(we, (float)r[0], ue);
+                uo = fmaf(wo, (float)r[1], uo);
+            }
+        }
+        z[al * kPad + fr * F + (int)(__brev((unsigned)m) >> (32 - logF))] = make_float2(ue, uo);
+    }
+    __syncthreads();
+    for (int half = 1, lh = 0; half < F; half <<= 1, ++lh) {
+        for (int jt = threadIdx.x; jt < n / 2; jt += kFThreads) {
+            const int tr = jt >> (logF - 1), j = jt & (F / 2 - 1);  // transform = (antenna, frame)
+            const int pos = j & (half - 1);
+            const int base = (tr >> (logPer - logF)) * kPad + (tr & (FR - 1)) * F;
+            const int i0 = base + ((j - pos) << 1) + pos, i1 = i0 + half;
+            const float2 b = cmul(z[i1], g_fetw[pos << (12 - lh)]);
+            const float2 x0 = z[i0];
+            z[i0] = cadd(x0, b);
+            z[i1] = csub(x0, b);
+        }
+        __syncthreads();
+    }
+    // unpack, calibrate, quantise; thread index: antenna fastest so that each
+    // (f, t) row of 16 antennas is one contiguous store
+    for (int idx = threadIdx.x; idx < n; idx += kFThreads) {
+        const int al = idx & (kFuseAnt - 1), rest = idx >> 4, fr = rest >> logF, f = rest & (F - 1);
+        const int64_t a = a0 + al, t = t0 + fr;
+        if (a >= N || t >= T) continue;
+        const float2* zz = z + al * kPad + fr * F;
+        const float2 zf = zz[f], zc = zz[(F - f) & (F - 1)];
+        const float2 e = make_float2(0.5f * (zf.x + zc.x), 0.5f * (zf.y - zc.y));
+        const float2 o = make_float2(0.5f * (zf.y + zc.y), -0.5f * (zf.x - zc.x));
+        const float2 x = cadd(e, cmul(o, g_fetw[f << tw_shift]));
+        const float2 g = gains ? __ldg(gains + (int64_t)f * N + a) : make_float2(1.f, 0.f);
+        const float2 y = calibrate(x, g, scale);
+        const int64_t oi = ((int64_t)f * T + t) * N + a;
+        if (I8) reinterpret_cast<char2*>(out)[oi] = make_char2(quantize8(y.x), quantize8(y.y));
+        else reinterpret_cast<float2*>(out)[oi] = y;
+    }
+}
+
+cudaError_t upload_fengine_twiddles() {
+    static float2 h[4096];
+    for (int j = 0; j < 4096; ++j) {
+        const double ang = -6.283185307179586476925286766559 * j / 8192.0;
+        h[j] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+    }
+    return cudaMemcpyToSymbol(g_fetw, h, sizeof h);
+}
+
 }  // namespace
 
 int64_t fengine_frames(int64_t n_samples, int32_t F, int32_t P) {
     const int64_t M = 2 * (int64_t)F;
     return n_samples >= (int64_t)(P - 1) * M ? (n_samples - (int64_t)(P - 1) * M) / M : 0;
+}
+
+int64_t fengine_scratch_bytes(int64_t N, int64_t S, int32_t F, int32_t P) {
+    if (F <= 256) return 0;  // the fused single pass needs no scratch
+    return (int64_t)sizeof(float2) * N * fengine_frames(S, F, P) * F;
+}
+
+int64_t fengine_ctas(int64_t N, int64_t T, int32_t F) {
+    if (F <= 256) {
+        const int FR = kFusePoints / (kFuseAnt * F);
+        return ((N + kFuseAnt - 1) / kFuseAnt) * ((T + FR - 1) / FR);
+    }
+    const int FR = std::max(1, kFPoints / F);
+    const int64_t frames_per_cta = std::max(FR, 32);
+    return std::max<int64_t>(N * ((T + frames_per_cta - 1) / frames_per_cta), ((F + 31) / 32) * ((N + 31) / 32) * T);
 }
 
 cudaError_t launch_fengine(const int8_t* raw, int64_t N, int64_t S, int32_t F, int32_t P,
@@ -141,6 +294,31 @@ cudaError_t launch_fengine(const int8_t* raw, int64_t N, int64_t S, int32_t F, i
     if (T <= 0 || N <= 0) return cudaSuccess;
     int logF = 0;
     while ((1 << logF) < F) ++logF;
+    if (F <= 256) {
+        static std::mutex mu;
+        static std::vector<int> done;
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        {
+            std::lock_guard<std::mutex> lock(mu);
+            if (std::find(done.begin(), done.end(), dev) == done.end()) {
+                if ((e = upload_fengine_twiddles()) != cudaSuccess) return e;
+                done.push_back(dev);
+            }
+        }
+        const unsigned ctas = (unsigned)fengine_ctas(N, T, F);
+        const bool vec = F >= 8 && S % 16 == 0 && (uintptr_t)raw % 16 == 0 && (uintptr_t)window % 16 == 0;
+        if (out_i8 && vec)
+            fengine_fused<true, true><<<ctas, kFThreads, 0, st>>>(raw, N, S, F, logF, P, window, T, gains, scale, out);
+        else if (out_i8)
+            fengine_fused<true, false><<<ctas, kFThreads, 0, st>>>(raw, N, S, F, logF, P, window, T, gains, scale, out);
+        else if (vec)
+            fengine_fused<false, true><<<ctas, kFThreads, 0, st>>>(raw, N, S, F, logF, P, window, T, gains, scale, out);
+        else
+            fengine_fused<false, false><<<ctas, kFThreads, 0, st>>>(raw, N, S, F, logF, P, window, T, gains, scale, out);
+        return cudaGetLastError();
+    }
     const int FR = std::max(1, kFPoints / F);
     const int frames_per_cta = std::max(FR, 32);
     const int64_t ctas = N * ((T + frames_per_cta - 1) / frames_per_cta);

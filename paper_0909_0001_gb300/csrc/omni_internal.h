@@ -101,6 +101,8 @@ int tc_stage_b_tile();  // level-1 frequencies per stage-B CTA
 // F-engine: frames per antenna, and the two launches (spectra into scratch
 // [N][T][F] float2, then calibrated, quantised or not, transposed to [F][T][N]).
 int64_t fengine_frames(int64_t n_samples, int32_t F, int32_t P);
+int64_t fengine_scratch_bytes(int64_t N, int64_t S, int32_t F, int32_t P);
+int64_t fengine_ctas(int64_t N, int64_t T, int32_t F);  // largest launch, CTAs
 cudaError_t launch_fengine(const int8_t* raw, int64_t N, int64_t S, int32_t F, int32_t P,
                            const float* window, const float2* gains, float scale, int out_i8,
                            void* out, float2* scratch, cudaStream_t stream);

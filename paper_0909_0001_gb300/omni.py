@@ -224,7 +224,8 @@ def fengine(raw: torch.Tensor, channels: int, taps: int = 1, window: Optional[to
     N, S = raw.shape
     L = load()
     need = L.omni_fengine_scratch_bytes(N, S, channels, taps)
-    T = need // (8 * N * channels) if need else 0
+    M = 2 * channels
+    T = (S - (taps - 1) * M) // M if S >= (taps - 1) * M else 0   # frames, as the library counts them
     if out is None:
         out = torch.empty((channels, T, N, 2), dtype=torch.int8 if dtype == "ci8" else torch.float32,
                           device=raw.device)

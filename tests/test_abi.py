@@ -163,5 +163,6 @@ def test_fengine_argument_checks_without_a_gpu(lib):
     assert f(None, 4, 64, 8, 1, None, None, 1.0, 7, None, None, 0, None, None) == 1     # bad dtype
     assert f(None, 4, 64, 32, 2, None, None, 1.0, 1, None, None, 0, None, None) == 0    # no frame
     assert f(None, 4, 64, 8, 1, None, None, 1.0, 1, None, None, 0, None, None) == 1     # NULL buffers
-    assert lib.omni_fengine_scratch_bytes(4, 2 * 8 * 5 + 3, 8, 1) == 8 * 4 * 5 * 8
-    assert lib.omni_fengine_scratch_bytes(4, 100, 64, 2) == 0
+    assert lib.omni_fengine_scratch_bytes(4, 2 * 512 * 5 + 3, 512, 1) == 8 * 4 * 5 * 512
+    assert lib.omni_fengine_scratch_bytes(4, 2 * 8 * 5 + 3, 8, 1) == 0       # fused pass, no scratch
+    assert lib.omni_fengine_scratch_bytes(4, 100, 1024, 2) == 0              # no frame

@@ -43,12 +43,13 @@ def test_fengine_matches_oracle(N, F, P, extra):
     assert relerr(Y, ref) <= TOL
 
 
-def test_fengine_int8_codes_are_the_quantised_floats():
+@pytest.mark.parametrize("F", [128, 512])      # the fused pass and the two-kernel pass
+def test_fengine_int8_codes_are_the_quantised_floats(F):
     rng = np.random.default_rng(7)
-    N, F, P, T = 9, 128, 4, 10
+    N, P, T = 9, 4, 10
     raw = torch.from_numpy(rng.integers(-128, 128, size=(N, (T + P - 1) * 2 * F)).astype(np.int8))
     w = (np.hanning(P * 2 * F) * np.sinc(np.linspace(-P / 2, P / 2, P * 2 * F))).astype(np.float32)
-    scale = 0.06
+    scale = 0.07 * (128 / F) ** 0.5
     Yf = run(raw, F, P, w, None, scale, "cf32")
     Yq = run(raw, F, P, w, None, scale, "ci8")
     f32 = np.stack([Yf.real, Yf.imag], axis=-1).astype(np.float32)
