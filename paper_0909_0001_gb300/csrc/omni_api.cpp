@@ -211,6 +211,8 @@ struct Knobs {
     int overlap = 1;              // overlap the two passes of consecutive chunks (OMNI_OVERLAP)
     int level_passes = 1;         // both axes of a square level in one pass (OMNI_LEVEL_PASSES)
     double split_tc = 0.0;        // mixed: share of a chunk's channels on tensor cores, 0 = all (OMNI_SPLIT_TC)
+    int tc_stage_a = 1;           // mixed: level 1 on tensor cores (1) or the FP32 FFT (0) (OMNI_TC_STAGE_A;
+                                  // measured on the 2-level workload: 20.8 vs 23.9 ms per step)
 };
 
 Knobs knobs_from_env() {
@@ -220,6 +222,7 @@ Knobs knobs_from_env() {
     if (const char* e = std::getenv("OMNI_OVERLAP")) k.overlap = std::atoi(e) != 0;
     if (const char* e = std::getenv("OMNI_LEVEL_PASSES")) k.level_passes = std::atoi(e) != 0;
     if (const char* e = std::getenv("OMNI_SPLIT_TC")) k.split_tc = std::atof(e);
+    if (const char* e = std::getenv("OMNI_TC_STAGE_A")) k.tc_stage_a = std::atoi(e) != 0;
     return k;
 }
 
@@ -387,6 +390,14 @@ omni_status build_passes(omni_plan* pl) {
         pb.inner = (int64_t)g.Lp[0] * g.Lp[1];
         pb.outer = 1;
         pb.W = pb.kind == KIND_TC_B ? tc_stage_b_tile() : 32;
+        if (!pl->knobs.tc_stage_a && pb.kind == KIND_TC_B) {
+            // level 1 as the FP32 FFT on CUDA cores, level 2 on tensor cores: the two
+            // passes of consecutive chunks then load different pipes
+            pa.L = g.Lp[0];
+            pa.n = g.n[0];
+            choose_level(pa);
+            pb.unscaled_in = 1;
+        }
         pl->fwd.push_back(pa);
         pl->fwd.push_back(pb);
         pl->fwd_elems = pa.outer * pa.q_out;
@@ -733,7 +744,8 @@ omni_status run_chunk(omni_plan* pl, const void* volts, int64_t vc0, int64_t Tsr
             b.S = cc_split;
             b.c0 = c0 + cc_tc;
             b.src = (const float2*)src + cc_tc * tc * src_stride;
-            b.fold_scale = 256.0;  // the tensor-core first pass scales the spectra by 1/16
+            // the tensor-core first pass scales the spectra by 1/16, the FP32 one does not
+            b.fold_scale = pl->fwd.front().kind == KIND_TC_A ? 256.0 : 1.0;
             a.S = cc_tc;
             OMNI_CUDA(cudaStreamWaitEvent(pl->split_stream, pl->mid_done[slot], 0), "cudaStreamWaitEvent");
             cudaError_t e2 = launch_counted(pl, (int)(pl->fwd.size() + pl->inv.size()), pl->split_pass, b,
@@ -959,14 +971,14 @@ std::string tune_key(const Geometry& g, omni_precision precision, omni_dtype dty
     std::string k;
     for (int d = 0; d < g.D; ++d) k += std::to_string(g.n[d]) + (d + 1 < g.D ? "x" : "");
     k += "|p" + std::to_string((int)precision) + "|d" + std::to_string((int)dtype) + "|C" +
-         std::to_string(C) + "|T" + std::to_string(T) + "|" + prop.name + "|v1";
+         std::to_string(C) + "|T" + std::to_string(T) + "|" + prop.name + "|v2";
     for (char& c : k)
         if (c == '"' || c == '\\' || c == '\n') c = '_';
     return k;
 }
 
 // One cache entry per line: {"key": "...", "chunk_mb": M, "chunk_channels": K,
-// "overlap": O, "level_passes": L, "split_tc": S, "ms": X}
+// "overlap": O, "level_passes": L, "split_tc": S, "tc_stage_a": A, "ms": X}
 bool tune_cache_read(const char* path, const std::string& key, Knobs& k) {
     if (!path) return false;
     FILE* f = std::fopen(path, "r");
@@ -981,14 +993,17 @@ bool tune_cache_read(const char* path, const std::string& key, Knobs& k) {
         int ov = 0, lp = 0;
         double sp = 0.0;
         const char* q = std::strstr(line, "\"chunk_mb\":");
+        int sa = 0;
         if (!q || std::sscanf(q, "\"chunk_mb\": %lld, \"chunk_channels\": %lld, \"overlap\": %d, "
-                                 "\"level_passes\": %d, \"split_tc\": %lf", &mb, &ch, &ov, &lp, &sp) != 5)
+                                 "\"level_passes\": %d, \"split_tc\": %lf, \"tc_stage_a\": %d",
+                              &mb, &ch, &ov, &lp, &sp, &sa) != 6)
             continue;
         t.chunk_mb = std::max<long long>(1, mb);
         t.chunk_channels = std::max<long long>(0, ch);
         t.overlap = ov != 0;
         t.level_passes = lp != 0;
         t.split_tc = sp;
+        t.tc_stage_a = sa != 0;
         k = t;
         found = true;  // the last matching line wins
     }
@@ -1001,9 +1016,9 @@ void tune_cache_write(const char* path, const std::string& key, const Knobs& k, 
     FILE* f = std::fopen(path, "a");
     if (!f) return;
     std::fprintf(f, "{\"key\": \"%s\", \"chunk_mb\": %lld, \"chunk_channels\": %lld, \"overlap\": %d, "
-                    "\"level_passes\": %d, \"split_tc\": %.3f, \"ms\": %.4f}\n",
+                    "\"level_passes\": %d, \"split_tc\": %.3f, \"tc_stage_a\": %d, \"ms\": %.4f}\n",
                  key.c_str(), (long long)k.chunk_mb, (long long)k.chunk_channels, k.overlap, k.level_passes,
-                 k.split_tc, ms);
+                 k.split_tc, k.tc_stage_a, ms);
     std::fclose(f);
 }
 
@@ -1035,14 +1050,16 @@ omni_status omni_plan_create_tuned(const omni_level* levels, int n_levels, int64
     for (int64_t mb : {384, 768, 1536, 3072})
         for (int ov : {1, 0}) {
             if (precision == OMNI_MIXED_FP16) {
-                for (double sp : {0.0, 0.3, 0.6}) {
-                    Knobs k;
-                    k.chunk_mb = mb;
-                    k.overlap = ov;
-                    k.split_tc = sp;
-                    if (sp > 0.0 && !ov) continue;  // the split needs the overlapped schedule
-                    cands.push_back(k);
-                }
+                for (int sa : {0, 1})
+                    for (double sp : {0.0, 0.3, 0.6}) {
+                        Knobs k;
+                        k.chunk_mb = mb;
+                        k.overlap = ov;
+                        k.split_tc = sp;
+                        k.tc_stage_a = sa;
+                        if (sp > 0.0 && !ov) continue;  // the split needs the overlapped schedule
+                        cands.push_back(k);
+                    }
             } else {
                 for (int lp : {1, 0}) {
                     Knobs k;

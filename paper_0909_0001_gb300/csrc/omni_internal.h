@@ -54,6 +54,7 @@ struct Pass {
     int L1, L2;     // KIND_SMEM split
     int W;          // KIND_SMEM / KIND_LEVEL: consecutive inner indices per unit
     int grid_cap;   // KIND_LEVEL finest MID: CTAs of the persistent kernel (0 = not used)
+    int unscaled_in;  // KIND_TC_B: level-1 spectra from the FP32 pass, not pre-scaled by 1/16
     int64_t inner, outer;
     const float2* tw;  // KIND_DIRECT: w_L^m = exp(-2 pi i m / L), m < L
 };
@@ -98,23 +99,25 @@ cudaError_t upload_tc_tables();
 cudaError_t tc_occupancy(int kind, int* blocks_per_sm);
 int tc_stage_b_tile();  // level-1 frequencies per stage-B CTA
 
-// F-engine: frames per antenna, and the two launches (spectra into scratch
-// [N][T][F] float2, then calibrated, quantised or not, transposed to [F][T][N]).
+cudaError_t launch_tc(const Pass& p, const PassArgs& a, cudaStream_t stream);
+cudaError_t upload_tc5_tables();
+cudaError_t tc5_occupancy(int* blocks_per_sm);
+cudaError_t launch_tc5(const Pass& p, const PassArgs& a, cudaStream_t stream);
+
+// Tile hybrid: cross-spectrum accumulation between the tiles' padded spectra.
+cudaError_t launch_xspec(const Pass& p, const PassArgs& a, cudaStream_t stream);
+cudaError_t xspec_occupancy(int* blocks_per_sm);
+int64_t xspec_ctas_per_channel(const Pass& p);
+
+// F-engine: frames per antenna, scratch bytes, CTAs of the largest launch, and
+// the launches (fused for F <= 256; else spectra into scratch [N][T][F], then
+// calibrated, quantised or not, transposed to [F][T][N]).
 int64_t fengine_frames(int64_t n_samples, int32_t F, int32_t P);
 int64_t fengine_scratch_bytes(int64_t N, int64_t S, int32_t F, int32_t P);
 int64_t fengine_ctas(int64_t N, int64_t T, int32_t F);  // largest launch, CTAs
 cudaError_t launch_fengine(const int8_t* raw, int64_t N, int64_t S, int32_t F, int32_t P,
                            const float* window, const float2* gains, float scale, int out_i8,
                            void* out, float2* scratch, cudaStream_t stream);
-
-// Tile hybrid: cross-spectrum accumulation between the tiles' padded spectra.
-cudaError_t launch_xspec(const Pass& p, const PassArgs& a, cudaStream_t stream);
-cudaError_t xspec_occupancy(int* blocks_per_sm);
-int64_t xspec_ctas_per_channel(const Pass& p);
-cudaError_t launch_tc(const Pass& p, const PassArgs& a, cudaStream_t stream);
-cudaError_t upload_tc5_tables();
-cudaError_t tc5_occupancy(int* blocks_per_sm);
-cudaError_t launch_tc5(const Pass& p, const PassArgs& a, cudaStream_t stream);
 
 // Set the calling thread's omni_last_error() message.
 void set_last_error(const char* msg);

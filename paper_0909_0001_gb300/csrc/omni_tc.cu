@@ -241,10 +241,14 @@ __global__ void __launch_bounds__(kB2Warps * 32, 4) tc_stage_b(Pass p, PassArgs 
         }
 #pragma unroll
         for (int q = 0; q < kB2KPW; ++q) {
-            // kA0 + q of blocks b0 (z0) and b0 + 1 (z1)
+            // kA0 + q of blocks b0 (z0) and b0 + 1 (z1), at the 1/16 scale stage A writes
             const float4 h0 = cur[q >> 1], h1 = cur[2 + (q >> 1)];
-            const float2 z0 = (q & 1) ? make_float2(h0.z, h0.w) : make_float2(h0.x, h0.y);
-            const float2 z1 = (q & 1) ? make_float2(h1.z, h1.w) : make_float2(h1.x, h1.y);
+            float2 z0 = (q & 1) ? make_float2(h0.z, h0.w) : make_float2(h0.x, h0.y);
+            float2 z1 = (q & 1) ? make_float2(h1.z, h1.w) : make_float2(h1.x, h1.y);
+            if (p.unscaled_in) {  // FP32 level-1 pass: apply the scale here (exact, 2^-4)
+                z0 = make_float2(z0.x * kScaleA, z0.y * kScaleA);
+                z1 = make_float2(z1.x * kScaleA, z1.y * kScaleA);
+            }
             uint32_t bh0, bl0, bh1, bl1;
             split2(z0.x, z1.x, bh0, bl0);  // rows re m3 = 2t, 2t+1
             split2(z0.y, z1.y, bh1, bl1);  // rows im m3

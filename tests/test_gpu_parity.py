@@ -315,6 +315,18 @@ def test_mixed_tcgen05_variant(monkeypatch):
     assert relerr_per_channel(V, default) <= 1e-6
 
 
+@pytest.mark.parametrize("stage_a", ["0", "1"])
+def test_mixed_level1_on_cuda_cores_or_tensor_cores(monkeypatch, stage_a):
+    """Level 1 as the FP32 FFT (0) or as split-FP16 GEMMs (1); level 2 on tensor
+    cores either way, with and without a split of the last pass."""
+    w = synth.workload("hier2")
+    x = synth.voltages(w, channels=5, samples=9)
+    monkeypatch.setenv("OMNI_TC_STAGE_A", stage_a)
+    check(w.levels, x, dtype="ci8", tol=TOL_MIXED, precision="mixed")
+    monkeypatch.setenv("OMNI_SPLIT_TC", "0.4")
+    check(w.levels, x, dtype="ci8", tol=TOL_MIXED, precision="mixed")
+
+
 @pytest.mark.parametrize("frac", ["0", "0.3", "0.5", "0.8"])
 def test_mixed_split_last_pass(monkeypatch, frac):
     """Channels of a chunk split between the tensor-core and the FP32 last pass
