@@ -1488,6 +1488,16 @@ omni_status omni_correlate_host(omni_plan* pl, const void* volts_host, int64_t T
     // staging buffer of chunk j-2 ('freed'); compute waits for 'ready'.
     OMNI_CUDA(cudaEventRecord(pl->freed[0], s), "cudaEventRecord");
     OMNI_CUDA(cudaEventRecord(pl->freed[1], s), "cudaEventRecord");
+    if (pl->overlap) {
+        // as in omni_correlate: the first pass of chunk j+1 (auxiliary stream)
+        // overlaps the last pass of chunk j; the auxiliary streams start after
+        // everything already queued on the caller's stream
+        OMNI_CUDA(cudaEventRecord(pl->start_ev, s), "cudaEventRecord");
+        OMNI_CUDA(cudaStreamWaitEvent(pl->aux_stream, pl->start_ev, 0), "cudaStreamWaitEvent");
+        if (pl->split)
+            OMNI_CUDA(cudaStreamWaitEvent(pl->split_stream, pl->start_ev, 0), "cudaStreamWaitEvent");
+        for (int b = 0; b < 2; ++b) OMNI_CUDA(cudaEventRecord(pl->last_done[b], s), "cudaEventRecord");
+    }
     // equal-sized chunks (no short tail chunk paying a whole fold and launch)
     const int64_t Cb = ceil_div(pl->C, ceil_div(pl->C, pl->Cc));
     const int64_t Tb = ceil_div(T, ceil_div(T, pl->Tc));
@@ -1505,8 +1515,10 @@ omni_status omni_correlate_host(omni_plan* pl, const void* volts_host, int64_t T
                           "cudaMemcpyAsync(H2D)");
             }
             OMNI_CUDA(cudaEventRecord(pl->ready[b], pl->copy_stream), "cudaEventRecord");
-            OMNI_CUDA(cudaStreamWaitEvent(s, pl->ready[b], 0), "cudaStreamWaitEvent");
-            st = run_chunk(pl, pl->stage[b], 0, tc, 0, c0, cc, tc, s);
+            // the first pass reads the staging buffer: on the auxiliary stream when overlapped
+            OMNI_CUDA(cudaStreamWaitEvent(pl->overlap ? pl->aux_stream : s, pl->ready[b], 0),
+                      "cudaStreamWaitEvent");
+            st = run_chunk(pl, pl->stage[b], 0, tc, 0, c0, cc, tc, s, pl->overlap ? b : -1);
             if (st != OMNI_OK) return st;
             OMNI_CUDA(cudaEventRecord(pl->freed[b], s), "cudaEventRecord");
         }
