@@ -18,6 +18,11 @@
 #include <unordered_map>
 #include <vector>
 
+namespace omni {
+// Resident CTAs per SM of a four-step LAST pass (omni_dispatch.cpp).
+cudaError_t smem_last_occupancy(const Pass& p, int src_kind, int* blocks_per_sm);
+}  // namespace omni
+
 using namespace omni;
 
 namespace {
@@ -515,6 +520,7 @@ void choose_chunks(omni_plan* pl) {
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, pl->device) != cudaSuccess) sms = 0;
     const int first_src = pl->fwd.size() == 1 ? (pl->dtype == OMNI_IN_CI8 ? SRC_CI8 : SRC_CF32) : SRC_BUF;
     if (last.kind == KIND_LEVEL && level_last_occupancy(last, first_src, &per_sm) != cudaSuccess) per_sm = 0;
+    if (last.kind == KIND_SMEM && smem_last_occupancy(last, first_src, &per_sm) != cudaSuccess) per_sm = 0;
     if (last.kind == KIND_TC_B && tc_occupancy(KIND_TC_B, &per_sm) != cudaSuccess) per_sm = 0;
     if (last.kind == KIND_TC5_B && tc5_occupancy(&per_sm) != cudaSuccess) per_sm = 0;
     if (last.kind == KIND_XSPEC && xspec_occupancy(&per_sm) != cudaSuccess) per_sm = 0;

@@ -16,6 +16,9 @@ cudaError_t launch_direct(const Pass& p, const PassArgs& a, cudaStream_t st);
 cudaError_t launch_level_a(const Pass& p, const PassArgs& a, cudaStream_t st);
 cudaError_t launch_level_b(const Pass& p, const PassArgs& a, cudaStream_t st);
 cudaError_t level_occupancy_a(int L, bool finest, int src_kind, int* out);
+cudaError_t smem_last_occupancy_a(const Pass& p, int src_kind, int* blocks_per_sm);
+cudaError_t smem_last_occupancy_b(const Pass& p, int src_kind, int* blocks_per_sm);
+cudaError_t smem_last_occupancy_c(const Pass& p, int src_kind, int* blocks_per_sm);
 cudaError_t level_occupancy_b(int L, bool finest, int src_kind, int* out);
 cudaError_t level_stream_occupancy_a(int L, int src_kind, int* out);
 cudaError_t level_stream_occupancy_b(int L, int src_kind, int* out);
@@ -40,6 +43,12 @@ cudaError_t launch_pass(const Pass& p, const PassArgs& a, cudaStream_t st) {
         case KIND_XSPEC: return launch_xspec(p, a, st);
         default: return launch_direct(p, a, st);
     }
+}
+
+cudaError_t smem_last_occupancy(const Pass& p, int src_kind, int* blocks_per_sm) {
+    return p.L <= 512 ? smem_last_occupancy_a(p, src_kind, blocks_per_sm)
+         : p.L <= 2048 ? smem_last_occupancy_b(p, src_kind, blocks_per_sm)
+                       : smem_last_occupancy_c(p, src_kind, blocks_per_sm);
 }
 
 cudaError_t level_last_occupancy(const Pass& p, int src_kind, int* blocks_per_sm) {

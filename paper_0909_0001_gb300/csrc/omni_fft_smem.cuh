@@ -141,6 +141,19 @@ cudaError_t launch_smem_t(const Pass& p, const PassArgs& a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// Resident CTAs per SM of the LAST-mode kernel of one four-step length.
+template <int L1, int L2>
+cudaError_t smem_last_occupancy_len(const Pass& p, int src_kind, int* blocks_per_sm) {
+    const int threads = p.W * L1;
+    const size_t smem = (size_t)p.W * (L1 * (L2 + 1) + 1) * sizeof(float2);
+    return dispatch_src<MODE_LAST>(src_kind, [&](auto S) {
+        auto k = pass_smem<L1, L2, MODE_LAST, decltype(S)::value>;
+        cudaError_t e = smem_limit_once((const void*)k, smem);
+        if (e != cudaSuccess) return e;
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, threads, smem);
+    });
+}
+
 // Every mode and source of one four-step length.
 template <int L1, int L2>
 cudaError_t launch_smem_len(const Pass& p, const PassArgs& a, cudaStream_t st) {

@@ -11,6 +11,14 @@ cudaError_t launch_smem_b(const Pass& p, const PassArgs& a, cudaStream_t st) {
     }
 }
 
+cudaError_t smem_last_occupancy_b(const Pass& p, int src_kind, int* blocks_per_sm) {
+    switch (p.L) {
+        case 1024: return smem_last_occupancy_len<32, 32>(p, src_kind, blocks_per_sm);
+        case 2048: return smem_last_occupancy_len<64, 32>(p, src_kind, blocks_per_sm);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 cudaError_t upload_twiddles_smem_b() { return upload_twiddles(); }
 
 }  // namespace omni

@@ -10,6 +10,13 @@ cudaError_t launch_smem_c(const Pass& p, const PassArgs& a, cudaStream_t st) {
     }
 }
 
+cudaError_t smem_last_occupancy_c(const Pass& p, int src_kind, int* blocks_per_sm) {
+    switch (p.L) {
+        case 4096: return smem_last_occupancy_len<64, 64>(p, src_kind, blocks_per_sm);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 cudaError_t upload_twiddles_smem_c() { return upload_twiddles(); }
 
 }  // namespace omni

@@ -166,3 +166,16 @@ def test_fengine_argument_checks_without_a_gpu(lib):
     assert lib.omni_fengine_scratch_bytes(4, 2 * 512 * 5 + 3, 512, 1) == 8 * 4 * 5 * 512
     assert lib.omni_fengine_scratch_bytes(4, 2 * 8 * 5 + 3, 8, 1) == 0       # fused pass, no scratch
     assert lib.omni_fengine_scratch_bytes(4, 100, 1024, 2) == 0              # no frame
+
+
+def test_library_has_no_unresolved_internal_symbols(lib):
+    """Every function the library calls inside itself is defined in it (an
+    internal declaration in the wrong namespace links as an undefined symbol)."""
+    import shutil
+    import subprocess
+    from paper_0909_0001_gb300.build import LIB
+    if shutil.which("nm") is None:
+        pytest.skip("nm not available")
+    out = subprocess.run(["nm", "-D", "--undefined-only", LIB], capture_output=True, text=True).stdout
+    bad = [l for l in out.splitlines() if "omni" in l or "_GLOBAL__N" in l]
+    assert not bad, bad
