@@ -155,6 +155,13 @@ __global__ void __launch_bounds__(kFThreads) fengine_fused(const int8_t* __restr
     // 16 antennas of an output row fall in different banks
     constexpr int kPad = kFusePoints / kFuseAnt + 1;
     __shared__ float2 z[kFuseAnt * kPad];
+    // this F's twiddles, from the table into shared memory once per CTA:
+    // stw[m] = e^{-2 pi i m / F} (m < F/2, the butterflies), utw[f] = e^{-i pi f / F}
+    __shared__ float2 stw[128], utw[256];
+    for (int j = threadIdx.x; j < F; j += kFThreads) {
+        if (j < F / 2) stw[j] = g_fetw[j << (13 - logF)];
+        utw[j] = g_fetw[j << (12 - logF)];
+    }
     // per antenna: FR frames x F points = 256 points; all index splits below
     // are shifts and masks (F is a power of two)
     constexpr int per = kFusePoints / kFuseAnt, logPer = 8, n = kFusePoints;
@@ -163,7 +170,6 @@ __global__ void __launch_bounds__(kFThreads) fengine_fused(const int8_t* __restr
     const int64_t a0 = (blockIdx.x / tchunks) * kFuseAnt;
     const int64_t t0 = (blockIdx.x % tchunks) * FR;
     const int64_t M = 2 * (int64_t)F;
-    const int tw_shift = 12 - logF;  // 4096 / F = 2^(12 - logF)
     // polyphase sums, packed (even, odd), bit-reversed within each frame.
     // VEC (rows 16-byte aligned, F >= 8): a thread takes 8 packed points, one
     // 16-byte load of samples and four of window weights per tap
@@ -230,7 +236,7 @@ __global__ void __launch_bounds__(kFThreads) fengine_fused(const int8_t* __restr
             const int pos = j & (half - 1);
             const int base = (tr >> (logPer - logF)) * kPad + (tr & (FR - 1)) * F;
             const int i0 = base + ((j - pos) << 1) + pos, i1 = i0 + half;
-            const float2 b = cmul(z[i1], g_fetw[pos << (12 - lh)]);
+            const float2 b = cmul(z[i1], stw[pos << (logF - 1 - lh)]);
             const float2 x0 = z[i0];
             z[i0] = cadd(x0, b);
             z[i1] = csub(x0, b);
@@ -247,7 +253,7 @@ __global__ void __launch_bounds__(kFThreads) fengine_fused(const int8_t* __restr
         const float2 zf = zz[f], zc = zz[(F - f) & (F - 1)];
         const float2 e = make_float2(0.5f * (zf.x + zc.x), 0.5f * (zf.y - zc.y));
         const float2 o = make_float2(0.5f * (zf.y + zc.y), -0.5f * (zf.x - zc.x));
-        const float2 x = cadd(e, cmul(o, g_fetw[f << tw_shift]));
+        const float2 x = cadd(e, cmul(o, utw[f]));
         const float2 g = gains ? __ldg(gains + (int64_t)f * N + a) : make_float2(1.f, 0.f);
         const float2 y = calibrate(x, g, scale);
         const int64_t oi = ((int64_t)f * T + t) * N + a;
