@@ -23,9 +23,20 @@ constexpr int kXJ = 16;  // tiles j per CTA, all of them per thread
 // CTA = (channel of the chunk, tile group i, tile chunk j, frequency tile);
 // thread = (frequency, tiles i = r and r + 8), 2 x 16 complex accumulators:
 // each spectrum value read from shared memory feeds two (or sixteen) products.
+// 8-byte asynchronous copy global -> shared (zero-filled when !valid).
+__device__ __forceinline__ void cp_async8(float2* dst, const float2* src, bool valid) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 8 : 0));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
 __global__ void __launch_bounds__(kXK * kXR, 2) xspec(Pass p, PassArgs a) {
-    __shared__ float2 sI[kXI][kXK];
-    __shared__ float2 sJ[kXJ][kXK];
+    // the next sample's tile is copied asynchronously into the other buffer
+    // while the current one is multiplied (no registers held for it)
+    __shared__ float2 sI[2][kXI][kXK];
+    __shared__ float2 sJ[2][kXJ][kXK];
     const int NT = (int)p.outer;
     const int64_t K = p.L;
     const int64_t ktiles = (K + kXK - 1) / kXK;
@@ -45,26 +56,39 @@ __global__ void __launch_bounds__(kXK * kXR, 2) xspec(Pass p, PassArgs a) {
     for (int h = 0; h < 2; ++h)
 #pragma unroll
         for (int jj = 0; jj < kXJ; ++jj) ar[h][jj] = ai[h][jj] = 0.f;
-    for (int ts = 0; ts < a.tc; ++ts) {
+    auto issue = [&](int ts) {
         const float2* Y = reinterpret_cast<const float2*>(a.src) + src_base(a, cc * a.tc + ts);
         const bool kin = k < K;
+        const int buf = ts & 1;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int ii = i0 + r + h * kXR, jr = j0 + r + h * kXR;
-            sI[r + h * kXR][kl] = (ii < NT && kin) ? __ldg(Y + (int64_t)ii * K + k) : make_float2(0.f, 0.f);
-            sJ[r + h * kXR][kl] = (jr < NT && kin) ? __ldg(Y + (int64_t)jr * K + k) : make_float2(0.f, 0.f);
+            const bool vi = ii < NT && kin, vj = jr < NT && kin;
+            cp_async8(&sI[buf][r + h * kXR][kl], vi ? Y + (int64_t)ii * K + k : Y, vi);
+            cp_async8(&sJ[buf][r + h * kXR][kl], vj ? Y + (int64_t)jr * K + k : Y, vj);
+        }
+        cp_async_commit();
+    };
+    if (a.tc > 0) issue(0);
+    for (int ts = 0; ts < a.tc; ++ts) {
+        if (ts + 1 < a.tc) {
+            issue(ts + 1);
+            cp_async_wait<1>();  // this sample's copies done, the next one's in flight
+        } else {
+            cp_async_wait<0>();
         }
         __syncthreads();
-        const float2 y0 = sI[r][kl], y1 = sI[r + kXR][kl];
+        const int buf = ts & 1;
+        const float2 y0 = sI[buf][r][kl], y1 = sI[buf][r + kXR][kl];
 #pragma unroll
         for (int jj = 0; jj < kXJ; ++jj) {
-            const float2 z = sJ[jj][kl];
+            const float2 z = sJ[buf][jj][kl];
             ar[0][jj] = fmaf(y0.x, z.x, fmaf(y0.y, z.y, ar[0][jj]));   // y conj(z)
             ai[0][jj] = fmaf(y0.y, z.x, fmaf(-y0.x, z.y, ai[0][jj]));
             ar[1][jj] = fmaf(y1.x, z.x, fmaf(y1.y, z.y, ar[1][jj]));
             ai[1][jj] = fmaf(y1.y, z.x, fmaf(-y1.x, z.y, ai[1][jj]));
         }
-        __syncthreads();
+        __syncthreads();  // the buffer is refilled two samples later
     }
     if (k >= K) return;
     double2* S = reinterpret_cast<double2*>(a.P + (a.c0 + cc) * a.P_stride);
