@@ -211,7 +211,7 @@ void omni::set_last_error(const char* msg) { g_last_error = msg; }
 // Tunable choices of a plan (the autotuner searches these; environment
 // variables override the defaults for experiments).
 struct Knobs {
-    int64_t chunk_mb = 1536;      // target size of each chunk scratch buffer (OMNI_CHUNK_MB)
+    int64_t chunk_mb = 3072;      // target size of each chunk scratch buffer (OMNI_CHUNK_MB)
     int64_t chunk_channels = 0;   // channels per chunk, 0 = one wave of the last pass (OMNI_CHUNK_CHANNELS)
     int overlap = 1;              // overlap the two passes of consecutive chunks (OMNI_OVERLAP)
     int level_passes = 1;         // both axes of a square level in one pass (OMNI_LEVEL_PASSES)
@@ -495,11 +495,11 @@ omni_status build_passes(omni_plan* pl) {
 }
 
 // Chunk sizes: the last pass gets one wave of resident CTAs (channels x inner
-// tiles), and each scratch buffer holds about chunk_mb MB of samples (1536;
-// OMNI_CHUNK_MB overrides):
+// tiles), and each scratch buffer holds about chunk_mb MB of samples (3072, the
+// autotuner's pick on the 2-level workload for both paths; OMNI_CHUNK_MB overrides):
 // long chunks amortise the FP64 fold and the launch ramp (measured on the
 // 2-level workload, FP32 path: 96 MB 33.7 ms, 192 MB 26.6, 384 MB 22.6,
-// 768 MB 21.3, 1536 MB 20.8 ms per step).
+// 768 MB 21.3, 1536 MB 20.8 ms per step; correlate alone, tuner: 3072 MB 20.25 ms).
 void choose_chunks(omni_plan* pl) {
     const int64_t mb = pl->knobs.chunk_mb;
     const int64_t target = mb << 20;
