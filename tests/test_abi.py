@@ -179,3 +179,23 @@ def test_library_has_no_unresolved_internal_symbols(lib):
     out = subprocess.run(["nm", "-D", "--undefined-only", LIB], capture_output=True, text=True).stdout
     bad = [l for l in out.splitlines() if "omni" in l or "_GLOBAL__N" in l]
     assert not bad, bad
+
+
+def test_beam_and_tuned_plan_errors_without_a_gpu(lib):
+    with pytest.raises(omni.OmniError) as e:          # one level: no coarser axes to correlate
+        omni.BeamPlan([synth.Level(8, 8)], 1)
+    assert e.value.status == 3
+    import ctypes
+    h = ctypes.c_void_p()
+    with pytest.raises(omni.OmniError) as e:          # the tuner needs voltages to time
+        omni._check(lib.omni_plan_create_tuned(omni._levels([synth.Level(4, 4)]), 1, 1, 0, 0, None, 1,
+                                                None, None, ctypes.byref(h)))
+    assert e.value.status == 1
+
+
+def test_fengine_wrapper_rejects_host_tensors():
+    import torch
+    with pytest.raises(ValueError):
+        omni.fengine(torch.zeros((4, 64), dtype=torch.int8), 8)
+    with pytest.raises(ValueError):
+        omni.fengine(torch.zeros((4, 64), dtype=torch.int16), 8)
