@@ -321,11 +321,13 @@ omni_status omni_sum_groups(const double* vis_dev, int64_t C, int64_t Q, const i
  * OMNI_ERR_UNSUPPORTED with the sizes in omni_last_error().
  *
  * The first call on each device does the set-up (uploads the twiddle tables
- * and looks up the array's device address), so make that first call before
- * any stream capture.  Every call shares the one array and the accumulator is
- * cleared at the start of each call: calls that overlap on the GPU (other
- * streams, other host threads) race on it and must be serialised by the
- * caller.  Synchronises stream before returning. */
+ * and looks up the array's device address); make that first call before any
+ * stream capture begins.  Every call also copies the direct-DFT twiddles
+ * (when the lattice has a non-power-of-two axis) from host memory and
+ * synchronises stream before returning.  Every call shares the one array and
+ * the accumulator is cleared at the start of each call: calls that overlap on
+ * the GPU (other streams, other host threads) race on it and must be
+ * serialised by the caller. */
 omni_status omni_correlate_noalloc(const omni_level* levels, int n_levels, int64_t n_channels,
                                    omni_dtype dtype, const void* volts_dev, int64_t T,
                                    double* vis_dev, void* stream);

@@ -291,23 +291,9 @@ struct omni_plan {
     std::vector<int64_t> array_lags;      // per array
 };
 
-namespace {
-
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-        if (prev != dev) cudaSetDevice(dev);
-    }
-    ~DeviceGuard() {
-        int cur = -1;
-        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-    }
-};
-
-int elem_bytes(omni_dtype t) { return t == OMNI_IN_CI8 ? 2 : 8; }
-
-void choose_kind(Pass& p) {
+// Kernel family and shared-memory split of one axis pass, from its length
+// (also used by omni_correlate_noalloc).
+void omni::choose_kind(Pass& p) {
     if (p.L == 1) {
         p.kind = KIND_DIRECT;
     } else if (is_pow2(p.L) && p.L >= 4 && p.L <= 64) {
@@ -329,6 +315,22 @@ void choose_kind(Pass& p) {
         p.kind = KIND_DIRECT;
     }
 }
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+int elem_bytes(omni_dtype t) { return t == OMNI_IN_CI8 ? 2 : 8; }
 
 // Level pass tiling (fixed at compile time in the kernels): the finest level
 // (inner == 1) packs whole blocks, W = 1; a coarser level takes W consecutive
@@ -394,8 +396,8 @@ omni_status build_passes(omni_plan* pl) {
         pb.q_out = g.Lp[2] * g.Lp[3];
         pb.inner = (int64_t)g.Lp[0] * g.Lp[1];
         pb.outer = 1;
-        pb.W = pb.kind == KIND_TC_B ? tc_stage_b_tile() : 32;
-        if (!pl->knobs.tc_stage_a && pb.kind == KIND_TC_B) {
+        pb.W = pb.kind == KIND_TC_B ? tc_stage_b_tile() : tc5_stage_b_tile();
+        if (!pl->knobs.tc_stage_a) {
             // level 1 as the FP32 FFT on CUDA cores, level 2 on tensor cores: the two
             // passes of consecutive chunks then load different pipes
             pa.L = g.Lp[0];

@@ -84,6 +84,10 @@ struct PassArgs {
 // Upload the twiddle tables to the current device (once per device).
 cudaError_t init_device_tables();
 
+// Kernel family of an axis pass from its length (register FFT up to 64 points,
+// four-step shared-memory FFT up to 4096, direct DFT otherwise).
+void choose_kind(Pass& p);
+
 // Launch one pass on stream.
 cudaError_t launch_pass(const Pass& p, const PassArgs& a, cudaStream_t stream);
 
@@ -102,6 +106,7 @@ int tc_stage_b_tile();  // level-1 frequencies per stage-B CTA
 cudaError_t launch_tc(const Pass& p, const PassArgs& a, cudaStream_t stream);
 cudaError_t upload_tc5_tables();
 cudaError_t tc5_occupancy(int* blocks_per_sm);
+int tc5_stage_b_tile();  // level-1 frequencies per tcgen05 stage-B CTA
 cudaError_t launch_tc5(const Pass& p, const PassArgs& a, cudaStream_t stream);
 
 // Tile hybrid: cross-spectrum accumulation between the tiles' padded spectra.

@@ -105,21 +105,7 @@ extern "C" omni_status omni_correlate_noalloc(const omni_level* levels, int n_le
     for (int d = 0; d < D; ++d)
         if (Lp[d] > 1) axes.push_back(d);
     if (axes.empty()) axes.push_back(0);
-    auto pow2 = [](int x) { return x > 0 && (x & (x - 1)) == 0; };
-    auto kind_of = [&](Pass& p) {
-        if (p.L > 1 && pow2(p.L) && p.L <= 64) {
-            p.kind = KIND_REG;
-        } else if (p.L > 64 && pow2(p.L)) {
-            p.kind = KIND_SMEM;
-            p.L1 = p.L >= 2048 ? 64 : (p.L >= 512 ? 32 : 16);
-            p.L2 = p.L / p.L1;
-            int W = 256 / p.L1;
-            while (W > 1 && W / 2 >= p.inner) W /= 2;
-            p.W = W;
-        } else {
-            p.kind = KIND_DIRECT;
-        }
-    };
+    // kernel family by axis length: the plan API's choice (choose_kind)
     std::vector<Pass> fwd, inv;
     int64_t fwd_elems = 0, inv_elems = 0, tw_floats = 0;
     for (size_t a = 0; a < axes.size(); ++a) {
@@ -133,7 +119,7 @@ extern "C" omni_status omni_correlate_noalloc(const omni_level* levels, int n_le
         for (int e = 0; e < d; ++e) p.inner *= Lp[e];
         for (int e = d + 1; e < D; ++e) p.outer *= n[e];
         p.mode = (a + 1 == axes.size()) ? MODE_LAST : MODE_MID;
-        kind_of(p);
+        choose_kind(p);
         if (p.mode == MODE_MID) fwd_elems = std::max(fwd_elems, p.outer * p.L * p.inner);
         if (p.kind == KIND_DIRECT) tw_floats += 2 * p.L;
         fwd.push_back(p);
@@ -150,7 +136,7 @@ extern "C" omni_status omni_correlate_noalloc(const omni_level* levels, int n_le
         for (int e = 0; e < d; ++e) p.inner *= Lp[e];
         for (int e = d + 1; e < D; ++e) p.outer *= 2 * n[e] - 1;
         p.mode = (a == 0) ? MODE_INV_LAST : MODE_INV_MID;
-        kind_of(p);
+        choose_kind(p);
         if (p.mode == MODE_INV_MID) inv_elems = std::max(inv_elems, p.outer * p.q_out * p.inner);
         if (p.kind == KIND_DIRECT) tw_floats += 2 * p.L;
         inv.push_back(p);

@@ -1,30 +1,31 @@
 // omni_tc5.cu -- stage B of the mixed-precision path on 5th-generation tensor
-// cores (tcgen05.mma, accumulators in tensor memory).
+// cores (tcgen05.mma: A operands and accumulators in tensor memory).
 //
-// Stage B takes the level-1 spectra Y[b][kA] (b = 8 m4 + m3 indexes the 8x8
+// Stage B takes the level-1 spectra Z[b][kA] (b = 8 m4 + m3 indexes the 8x8
 // grid of blocks, kA the 32x32 level-1 frequencies, scaled by 1/16) and, for
 // every kA, computes the padded 2-D DFT over the level-2 grid (8x8 -> 16x16),
 // squares it and sums over the chunk's samples (Sec. II.C's |FFT|^2 summed over
-// time; Appendix A step 5).  A CTA owns 16 consecutive kA and, per sample, runs
-// two batched real GEMMs of M = 128, N = 32, K = 16 on FP16 hi/lo operands:
-//   GEMM 3: rows (kA, m4):  D2 = [Zr | Zi] . V16        (1 tile  x 3 terms)
-//   GEMM 4: rows (kA, k3):  D3 = [D2r | D2i]^T . V16    (2 tiles x 3 terms)
-// with V16 = [[Vr, Vi], [-Vi, Vr]], V[m][k] = exp(-2 pi i m k / 16), K rows
-// (re m | im m), N columns (re k | im k).  Between the GEMMs the threads read D2
-// out of tensor memory, split it into FP16 hi/lo and write it transposed (rows
-// (kA, k3), K = m4) into shared memory as GEMM 4's A operand.  |D3|^2 is summed
-// in registers over the samples and folded into FP64 once per chunk.
-// The samples are software-pipelined: GEMM 3 of sample t+1 is issued together
-// with GEMM 4 of sample t, so each sample costs one MMA round trip and one CTA
-// barrier; 128 tensor-memory columns per CTA let four CTAs share an SM.
+// time; Appendix A step 5).  A CTA owns 16 consecutive kA of one channel and,
+// per sample, runs two real GEMMs of M = 128, N = 32, K = 16 on FP16 hi/lo
+// operands (three products hi*hi + lo*hi + hi*lo, FP32 accumulation):
+//   GEMM 3: rows (kA, m4):  D3 = [Zr | Zi] . V16           (1 row tile)
+//   GEMM 4: rows (kA, k3):  D4 = [D3r | D3i]^T . V16       (2 row tiles)
+// with V16 = [[Vr, Vi], [-Vi, Vr]], V[m][k] = exp(-2 pi i m k / 16): K rows
+// (re m | im m), N columns (re k | im k).
 //
-// Operands sit in shared memory in the no-swizzle K-major layout: 8-row x
-// 16-byte core matrices, K-adjacent core matrices 144 bytes apart (leading
-// byte offset), 8-row groups 272 bytes apart (stride byte offset).  The 16-byte
-// paddings put the 32 words a warp writes when it transposes D2 into 32
-// distinct shared-memory banks.  Every wait
-// on an MMA completion is bounded; on expiry the CTA sets the plan's error word,
-// frees its tensor memory and returns.
+// The A operands live in tensor memory: each thread owns one row (one line of
+// the transform), splits it into FP16 hi/lo and writes it with tcgen05.st, so
+// the MMAs read only the 1 KB B tables from shared memory.  Between the GEMMs
+// the D3 rows (lines (kA, m4)) are turned into GEMM 4's rows (lines (kA, k3))
+// through a padded FP32 shared-memory buffer (the 2-D DFT's transpose).  The
+// samples are software-pipelined: while GEMM 4 of sample t and GEMM 3 of sample
+// t+1 run, the threads split and store sample t+2's GEMM-3 operand (double
+// buffered) and square sample t-1's GEMM-4 output (double buffered).  |D4|^2
+// is summed in registers over the chunk and folded into FP64 once.
+//
+// Every wait on an MMA completion is bounded; on expiry the CTA sets the
+// plan's error word, waits (bounded) for its in-flight MMAs, frees its tensor
+// memory and returns.
 #include "omni_fft_common.cuh"
 
 #include <cuda_fp16.h>
@@ -35,15 +36,28 @@
 namespace omni {
 namespace {
 
-constexpr int kT5Tile = 16;           // level-1 frequencies per CTA
-constexpr int kT5Threads = 128;
-constexpr int kLBO = 144;             // bytes between K-adjacent core matrices
-constexpr int kSBO = 272;             // bytes between 8-row groups
-constexpr int kTileBytes = 16 * kSBO; // one M = 128, K = 16 FP16 operand tile
-constexpr int kBBytes = 4 * kSBO;     // the N = 32, K = 16 B operand
-constexpr int kTmemCols = 128;        // D2: columns 0..31, D3: two tiles at 32..95
-constexpr double kT5Fold = 256.0;     // undoes stage A's 1/16 scale, squared
-constexpr int kFoldPitch = 257;       // floats per kA row of the fold staging
+constexpr int kT5Tile = 16;            // level-1 frequencies per CTA
+constexpr int kT5Threads = 128;        // threads per warpgroup: one per tensor-memory lane
+constexpr int kLBO = 144;              // B table: bytes between K-adjacent core matrices
+constexpr int kSBO = 272;              // B table: bytes between 8-row groups
+constexpr int kBBytes = 4 * kSBO;      // the N = 32, K = 16 B operand
+constexpr uint32_t kTmemCols = 256;    // two CTAs per SM
+constexpr double kT5Fold = 256.0;      // undoes stage A's 1/16 scale, squared
+constexpr float kScale16 = 1.0f / 16.0f;
+// tensor-memory columns
+constexpr uint32_t kColA3 = 0;         // GEMM-3 operand, two slots of 16: hi (8) + lo (8)
+constexpr uint32_t kColD3 = 32;        // GEMM-3 result, 32
+constexpr uint32_t kColA4 = 64;        // GEMM-4 operand, two slots x two row tiles of 16
+constexpr uint32_t kColD4 = 128;       // GEMM-4 result, two slots x two tiles x 32
+// transpose buffer [kA_l][k3][m4] float2; rows of one kA_l padded by 16 bytes
+// so that both the writes (lines (kA, m4)) and the reads (lines (kA, k3)) take
+// the minimum number of shared-memory wavefronts
+constexpr int kXRow = 16 * 8 * 8 + 16;
+constexpr int kXBytes = 16 * kXRow;
+// dynamic shared memory: the B tables, the transpose buffer, and padding that
+// keeps at most two CTAs on an SM (two x 256 tensor-memory columns)
+constexpr size_t kT5Smem = 80 * 1024;
+static_assert(2 * kBBytes + kXBytes <= (int)kT5Smem, "stage-B shared memory");
 
 // B operand (V16 real form) hi and lo, already in the shared-memory layout.
 __device__ __align__(16) unsigned char g_t5B[2][kBBytes];
@@ -62,13 +76,14 @@ __device__ __forceinline__ uint64_t sdesc(const void* p) {
            ((uint64_t)(kSBO >> 4) << 32) | ((uint64_t)1 << 46);
 }
 
-// kind::f16, FP32 accumulate, FP16 A and B, both K-major, N = 32, M = 128
+// kind::f16, FP32 accumulate, FP16 A and B, K-major, N = 32, M = 128
 constexpr uint32_t kIdesc = (1u << 4) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
 
-__device__ __forceinline__ void mma_t5(uint32_t d, uint64_t a, uint64_t b, int acc) {
+// D[d] (+)= A[a] . B: A from tensor memory (row = lane, K = 16 FP16 in 8 columns)
+__device__ __forceinline__ void mma_ta(uint32_t d, uint32_t a, uint64_t b, int acc) {
     asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                 " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-                 :: "r"(d), "l"(a), "l"(b), "r"(kIdesc), "r"(acc));
+                 " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n"
+                 :: "r"(d), "r"(a), "l"(b), "r"(kIdesc), "r"(acc));
 }
 
 __device__ __forceinline__ void commit_t5(uint64_t* bar) {
@@ -108,36 +123,82 @@ __device__ __forceinline__ void ld32(uint32_t taddr, float (&v)[32]) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ uint32_t pack_h2(__half lo, __half hi) {
-    uint16_t a, b;
-    memcpy(&a, &lo, 2);
-    memcpy(&b, &hi, 2);
-    return (uint32_t)a | ((uint32_t)b << 16);
+__device__ __forceinline__ void st16(uint32_t taddr, const uint32_t (&r)[16]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+                 "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};"
+                 :: "r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]),
+                    "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]),
+                    "r"(r[13]), "r"(r[14]), "r"(r[15]));
+}
+
+__device__ __forceinline__ uint32_t h2u(__half2 h) {
+    uint32_t u;
+    memcpy(&u, &h, 4);
+    return u;
+}
+
+// (x0, x1) -> hi = fp16(x), lo = fp16(x - hi), packed with x0 in the low half
+// (the even K element of a tensor-memory column).
+__device__ __forceinline__ void split2(float x0, float x1, uint32_t& hi, uint32_t& lo) {
+    const __half2 h = __floats2half2_rn(x0, x1);
+    const float2 hf = __half22float2(h);
+    hi = h2u(h);
+    lo = h2u(__floats2half2_rn(x0 - hf.x, x1 - hf.y));
+}
+
+// Eight complex values (one line, K = re 0..7 | im 0..7) -> the 16 columns of a
+// tensor-memory A row: hi words 0..7, lo words 8..15.
+__device__ __forceinline__ void split_row(const float2 (&z)[8], float s, uint32_t (&r)[16]) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        split2(z[2 * q].x * s, z[2 * q + 1].x * s, r[q], r[8 + q]);
+        split2(z[2 * q].y * s, z[2 * q + 1].y * s, r[4 + q], r[12 + q]);
+    }
 }
 
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;"); }
 __device__ __forceinline__ void tc_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;"); }
 __device__ __forceinline__ void tc_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;"); }
 
-__global__ void __launch_bounds__(kT5Threads, 4) tc5_stage_b(Pass p, PassArgs a) {
+__device__ __forceinline__ void mbar_init(uint64_t* bar, int count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" :: "r"(smem_u32(bar)));
+}
+// Warpgroup 0's own barrier (id 1, 128 threads), OR-reducing a flag.
+__device__ __forceinline__ bool wg0_sync_or(bool v) {
+    uint32_t r;
+    asm volatile("{\n .reg .pred p, q;\n setp.ne.b32 q, %1, 0;\n"
+                 " barrier.cta.red.or.pred p, 1, 128, q;\n selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(r) : "r"((int)v));
+    return r != 0;
+}
+
+// Two warpgroups with one tensor-memory lane each per thread (lane = tid % 128):
+// warpgroup 0 turns D3 into the GEMM-4 operand (the transpose) and issues all
+// MMAs; warpgroup 1 loads and splits the voltages' level-1 spectra into the
+// GEMM-3 operand and squares the GEMM-4 results.  They hand off through
+// mbarriers on double-buffered tensor-memory slots (full: written, empty:
+// consumed); GEMM 3 of sample t+1 is issued before the transpose of sample t,
+// so it runs while warpgroup 0 works.
+__global__ void __launch_bounds__(2 * kT5Threads, 2) tc5_stage_b(Pass p, PassArgs a) {
     extern __shared__ __align__(1024) unsigned char dsm[];
-    unsigned char* a3h = dsm;                      // 1 tile
-    unsigned char* a3l = dsm + 1 * kTileBytes;
-    unsigned char* a4h = dsm + 2 * kTileBytes;     // 2 tiles
-    unsigned char* a4l = dsm + 4 * kTileBytes;
-    unsigned char* bh = dsm + 6 * kTileBytes;
-    unsigned char* bl = bh + kBBytes;
-    float* sfold = reinterpret_cast<float*>(dsm);  // after the last sample
-    __shared__ __align__(8) uint64_t mbar;
-    __shared__ __align__(8) uint64_t never_bar;  // test hook: a barrier nothing arrives on
+    unsigned char* bh = dsm;
+    unsigned char* bl = dsm + kBBytes;
+    unsigned char* xbuf = dsm + 2 * kBBytes;
+    __shared__ __align__(8) uint64_t a3_full[2], a3_empty[2], d3_full, d4_full[2], d4_empty[2];
+    __shared__ __align__(8) uint64_t drain, never_bar;  // never_bar: test hook, nothing arrives
     __shared__ uint32_t tmem_slot;
 
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int wg = tid >> 7, ltid = tid & 127;
     const int64_t tiles = p.inner / kT5Tile;
     const int64_t cc = blockIdx.x / tiles;
     const int64_t kA0 = (blockIdx.x - cc * tiles) * kT5Tile;
     const int64_t s0 = cc * a.tc;
     const int tc = a.tc;
+    const long long budget = a.force_expire ? kTestWaitCycles : kWaitCycles;
 
     for (int i = tid; i < 2 * kBBytes / 16; i += blockDim.x)
         reinterpret_cast<uint4*>(bh)[i] = reinterpret_cast<const uint4*>(&g_t5B[0][0])[i];
@@ -147,170 +208,192 @@ __global__ void __launch_bounds__(kT5Threads, 4) tc5_stage_b(Pass p, PassArgs a)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mbar)));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&never_bar)));
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&a3_full[i], kT5Threads);
+            mbar_init(&a3_empty[i], 1);
+            mbar_init(&d4_full[i], 1);
+            mbar_init(&d4_empty[i], kT5Threads);
+        }
+        mbar_init(&d3_full, 1);
+        mbar_init(&drain, 1);
+        mbar_init(&never_bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
+    fence_async_smem();
     tc_before_sync();
     __syncthreads();
     tc_after_sync();
     const uint32_t tmem = tmem_slot;
-    const uint32_t lane_base = (uint32_t)(32 * warp) << 16;  // this warp's tensor-memory lanes
-    uint32_t parity = 0;
+    const uint32_t row = tmem + ((uint32_t)(32 * (warp & 3)) << 16);  // this thread's lane
+    // GEMM-3 line of this thread's lane: (kA_l, m4), a half-warp holding two m4
+    // x eight kA_l so that its transpose stores hit 16 distinct bank pairs;
+    // GEMM-4 lines: (kA_l, k3) = (ltid % 16, 8 j + ltid / 16), j = 0, 1
+    const int h16 = ltid >> 4;
+    const int a_kl = (ltid & 7) + 8 * (h16 & 1), a_m4 = 2 * (h16 >> 1) + ((ltid >> 3) & 1);
+    const int kl = ltid & 15, hi4 = ltid >> 4;
     bool aborted = false;
 
-    // GEMM 3 input: thread = (kA_l, m4), the 8 values Z[m4][m3] of one kA
-    const int kl_in = 4 * warp + (lane >> 3), m4_in = lane & 7;
-    float2 pre[8];
-    auto fetch = [&](int64_t s) {
-        const float2* base = reinterpret_cast<const float2*>(a.src) + src_base(a, s) + kA0 + kl_in;
+    if (wg == 1 && tc > 0) {
+        // ---- warpgroup 1: GEMM-3 operands in, |GEMM-4|^2 out
+        // GEMM-3 line (kA_l, m4): Z[8 m4 + m3][kA], m3 = 0..7 (a warp reads two
+        // 128-byte runs per m3)
+        const float in_scale = p.unscaled_in ? kScale16 : 1.0f;
+        const float2* zline = reinterpret_cast<const float2*>(a.src) + kA0 + a_kl + (int64_t)(8 * a_m4) * p.inner;
+        float2 pre[8];
+        auto fetch = [&](int64_t s) {
+            const float2* b = zline + src_base(a, s);
 #pragma unroll
-        for (int m3 = 0; m3 < 8; ++m3) pre[m3] = base[(int64_t)(8 * m4_in + m3) * p.inner];
-    };
-    // A operand of GEMM 3: row 8 kA_l + m4, K = (re m3 | im m3), hi and lo
-    auto write_a3 = [&]() {
-        const int off = tile_off(8 * kl_in + m4_in, 0);
-        uint32_t hr[4], lr[4], hi_[4], li[4];
+            for (int m3 = 0; m3 < 8; ++m3) pre[m3] = __ldg(b + (int64_t)m3 * p.inner);
+        };
+        float acc[2][16];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const float2 z0 = pre[2 * q], z1 = pre[2 * q + 1];
-            const __half h0 = __float2half_rn(z0.x), h1 = __float2half_rn(z1.x);
-            const __half g0 = __float2half_rn(z0.y), g1 = __float2half_rn(z1.y);
-            hr[q] = pack_h2(h0, h1);
-            lr[q] = pack_h2(__float2half_rn(z0.x - __half2float(h0)), __float2half_rn(z1.x - __half2float(h1)));
-            hi_[q] = pack_h2(g0, g1);
-            li[q] = pack_h2(__float2half_rn(z0.y - __half2float(g0)), __float2half_rn(z1.y - __half2float(g1)));
-        }
-        *reinterpret_cast<uint4*>(a3h + off) = make_uint4(hr[0], hr[1], hr[2], hr[3]);
-        *reinterpret_cast<uint4*>(a3h + off + kLBO) = make_uint4(hi_[0], hi_[1], hi_[2], hi_[3]);
-        *reinterpret_cast<uint4*>(a3l + off) = make_uint4(lr[0], lr[1], lr[2], lr[3]);
-        *reinterpret_cast<uint4*>(a3l + off + kLBO) = make_uint4(li[0], li[1], li[2], li[3]);
-    };
-    // D2 row (kA_l, m4) of this thread -> GEMM 4's A operand rows (kA_l, k3), K = (re m4 | im m4)
-    auto d2_to_a4 = [&]() {
-        float v[32];
-        ld32(tmem + lane_base, v);
-        const int r = 32 * warp + lane;
-        const int kl = r >> 3, m4 = r & 7;
-        const bool even = (m4 & 1) == 0;
+        for (int j = 0; j < 2; ++j)
 #pragma unroll
-        for (int k3 = 0; k3 < 16; ++k3) {
-            const float re = v[k3], im = v[16 + k3];
-            const float pre_ = __shfl_xor_sync(0xffffffffu, re, 1);
-            const float pim = __shfl_xor_sync(0xffffffffu, im, 1);
-            // even lanes write the real pair (K = m4, m4+1), odd lanes the imaginary pair
-            const float x0 = even ? re : pim, x1 = even ? pre_ : im;
-            const int k0 = even ? m4 : 8 + m4 - 1;
-            const int R = 16 * kl + k3;
-            const int off = (R >> 7) * kTileBytes + tile_off(R & 127, k0);
-            const __half h0 = __float2half_rn(x0), h1 = __float2half_rn(x1);
-            *reinterpret_cast<uint32_t*>(a4h + off) = pack_h2(h0, h1);
-            *reinterpret_cast<uint32_t*>(a4l + off) =
-                pack_h2(__float2half_rn(x0 - __half2float(h0)), __float2half_rn(x1 - __half2float(h1)));
-        }
-    };
-    auto issue_gemm3 = [&]() {
-        const uint64_t dbh = sdesc(bh), dbl = sdesc(bl);
-        mma_t5(tmem, sdesc(a3h), dbh, 0);
-        mma_t5(tmem, sdesc(a3l), dbh, 1);
-        mma_t5(tmem, sdesc(a3h), dbl, 1);
-    };
-    auto issue_gemm4 = [&]() {
-        const uint64_t dbh = sdesc(bh), dbl = sdesc(bl);
-#pragma unroll
-        for (int m = 0; m < 2; ++m) {
-            const uint32_t d = tmem + 32 + 32 * m;
-            mma_t5(d, sdesc(a4h + m * kTileBytes), dbh, 0);
-            mma_t5(d, sdesc(a4l + m * kTileBytes), dbh, 1);
-            mma_t5(d, sdesc(a4h + m * kTileBytes), dbl, 1);
-        }
-    };
-    // handshake: threads' shared-memory operands -> MMA issue
-    auto to_mma = [&]() {
-        fence_async_smem();
-        tc_before_sync();
-        __syncthreads();
-        tc_after_sync();
-    };
-    float acc[2][16];
-#pragma unroll
-    for (int j = 0; j < 2; ++j)
-#pragma unroll
-        for (int k = 0; k < 16; ++k) acc[j][k] = 0.f;
-
-    // prologue: GEMM 3 of sample 0, A4(0) and A3(1) ready
-    fetch(s0);
-    write_a3();
-    if (tc > 1) fetch(s0 + 1);
-    to_mma();
-    if (tid == 0) {
-        issue_gemm3();
-        commit_t5(&mbar);
-    }
-    {
-        // test hook: wait on a barrier that nothing arrives on, with a short budget
-        const bool ok = a.force_expire ? wait_t5(&never_bar, 0, kTestWaitCycles)
-                                       : wait_t5(&mbar, parity);
-        parity ^= 1;
-        if (__syncthreads_or(!ok)) aborted = true;
-    }
-    if (!aborted) {
-        tc_after_sync();
-        d2_to_a4();
-        if (tc > 1) {
-            write_a3();
-            if (tc > 2) fetch(s0 + 2);
-        }
-        to_mma();
-        for (int t = 0; t < tc; ++t) {
-            // GEMM 3 of sample t+1 and GEMM 4 of sample t in flight together
-            if (tid == 0) {
-                if (t + 1 < tc) issue_gemm3();
-                issue_gemm4();
-                commit_t5(&mbar);
-            }
-            const bool ok = wait_t5(&mbar, parity);
-            parity ^= 1;
-            if (__syncthreads_or(!ok)) { aborted = true; break; }
+            for (int k = 0; k < 16; ++k) acc[j][k] = 0.f;
+        auto square = [&](int t) {  // |D4|^2 of sample t, then release its slot
+            const int sl = t & 1;
+            // warp-uniform verdicts: the tcgen05.ld below is .sync.aligned
+            if (!__all_sync(0xffffffffu, wait_t5(&d4_full[sl], (t >> 1) & 1, budget))) return false;
             tc_after_sync();
 #pragma unroll
-            for (int j = 0; j < 2; ++j) {  // |D3|^2 of sample t
+            for (int j = 0; j < 2; ++j) {
                 float v[32];
-                ld32(tmem + lane_base + 32 + 32 * j, v);
+                ld32(row + kColD4 + 64 * sl + 32 * j, v);
 #pragma unroll
                 for (int k4 = 0; k4 < 16; ++k4)
                     acc[j][k4] = fmaf(v[k4], v[k4], fmaf(v[16 + k4], v[16 + k4], acc[j][k4]));
             }
-            if (t + 1 < tc) d2_to_a4();   // A4(t+1)
-            if (t + 2 < tc) {             // A3(t+2), next voltages in flight
-                write_a3();
-                if (t + 3 < tc) fetch(s0 + t + 3);
+            tc_before_sync();
+            mbar_arrive(&d4_empty[sl]);
+            return true;
+        };
+        fetch(s0);
+        for (int t = 0; t < tc && !aborted; ++t) {
+            const int sl = t & 1;
+            if (t >= 2 && !__all_sync(0xffffffffu, wait_t5(&a3_empty[sl], ((t >> 1) - 1) & 1, budget))) {
+                aborted = true;
+                break;
             }
-            to_mma();
+            uint32_t r[16];
+            split_row(pre, in_scale, r);
+            if (t + 1 < tc) fetch(s0 + t + 1);
+            st16(row + kColA3 + 16 * sl, r);
+            asm volatile("tcgen05.wait::st.sync.aligned;");
+            tc_before_sync();
+            mbar_arrive(&a3_full[sl]);
+            if (t >= 1 && !square(t - 1)) aborted = true;
         }
-    }
-    if (aborted) {
-        // the MMA that did not complete may still be in flight: wait once more
-        // (bounded) before the tensor memory is freed
-        if (tid == 0) {
+        if (!aborted && !square(tc - 1)) aborted = true;
+        if (aborted) {
             atomicExch(a.err, 1);
-            wait_t5(&mbar, parity ^ 1);
-        }
-    } else {
-        // fold through shared memory so the FP64 updates run along kA
+        } else {
+            // fold: lines (kA_l, k3 = 8 j + ltid / 16); P row 16 k4 + k3, a warp
+            // writes two 128-byte runs of kA per (j, k4)
+            double* P = a.P + (a.c0 + cc) * a.P_stride + kA0 + kl;
 #pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            const int R = 128 * j + 32 * warp + lane;  // (kA_l, k3) row
-            const int kl = R >> 4, k3 = R & 15;
+            for (int j = 0; j < 2; ++j) {
+                const int k3 = 8 * j + hi4;
 #pragma unroll
-            for (int k4 = 0; k4 < 16; ++k4) sfold[kl * kFoldPitch + k4 * 16 + k3] = acc[j][k4];
+                for (int k4 = 0; k4 < 16; ++k4)
+                    P[(int64_t)(16 * k4 + k3) * p.inner] += kT5Fold * (double)acc[j][k4];
+            }
         }
-        __syncthreads();
-        double* P = a.P + (a.c0 + cc) * a.P_stride;
-        for (int e = tid; e < 256 * kT5Tile; e += blockDim.x) {
-            const int kl = e % kT5Tile, row = e / kT5Tile;  // row = k4 * 16 + k3
-            P[(int64_t)row * p.inner + kA0 + kl] += kT5Fold * (double)sfold[kl * kFoldPitch + row];
+    } else if (wg == 0 && tc > 0) {
+        // ---- warpgroup 0: D3 -> transpose -> GEMM-4 operand; issues every MMA
+        const uint64_t dbh = sdesc(bh), dbl = sdesc(bl);
+        auto issue_gemm3 = [&](int sl) {
+            const uint32_t d = tmem + kColD3, ah = tmem + kColA3 + 16 * sl, al = ah + 8;
+            mma_ta(d, ah, dbh, 0);
+            mma_ta(d, al, dbh, 1);
+            mma_ta(d, ah, dbl, 1);
+            commit_t5(&a3_empty[sl]);
+            commit_t5(&d3_full);
+        };
+        bool bad = false;
+        if (ltid == 0) {
+            bad = !wait_t5(&a3_full[0], 0, budget);
+            if (!bad) {
+                tc_after_sync();
+                issue_gemm3(0);
+            }
         }
+        aborted = wg0_sync_or(bad);
+        float2* xw = reinterpret_cast<float2*>(xbuf + a_kl * kXRow) + a_m4;
+        bad = false;  // thread 0: a wait before an MMA issue expired
+        for (int t = 0; t < tc && !aborted; ++t) {
+            const int sl = t & 1;
+            // D3 of sample t (GEMM 4 of sample t-2 is complete too: issued earlier)
+            const bool ok = (a.force_expire && t == 0) ? wait_t5(&never_bar, 0, kTestWaitCycles)
+                                                       : wait_t5(&d3_full, t & 1, budget);
+            if (wg0_sync_or(!ok || bad)) {
+                aborted = true;
+                break;
+            }
+            tc_after_sync();
+            float v[32];
+            ld32(row + kColD3, v);
+            tc_before_sync();
+            // every D3 row read: GEMM 3 of sample t+1 may overwrite it
+            asm volatile("barrier.cta.sync 1, 128;");
+            if (ltid == 0 && t + 1 < tc) {
+                tc_after_sync();
+                bad = !wait_t5(&a3_full[(t + 1) & 1], ((t + 1) >> 1) & 1, budget);
+                if (!bad) {
+                    tc_after_sync();
+                    issue_gemm3((t + 1) & 1);
+                }
+            }
+            // transpose through shared memory: D3 rows (kA_l, m4) -> GEMM-4 rows (kA_l, k3)
+#pragma unroll
+            for (int k3 = 0; k3 < 16; ++k3) xw[8 * k3] = make_float2(v[k3], v[16 + k3]);
+            asm volatile("barrier.cta.sync 1, 128;");
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const float4* xr = reinterpret_cast<const float4*>(xbuf + kl * kXRow + (8 * j + hi4) * 64);
+                float2 z[8];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float4 f = xr[q];
+                    z[2 * q] = make_float2(f.x, f.y);
+                    z[2 * q + 1] = make_float2(f.z, f.w);
+                }
+                uint32_t r[16];
+                split_row(z, 1.0f, r);
+                st16(row + kColA4 + 32 * sl + 16 * j, r);
+            }
+            asm volatile("tcgen05.wait::st.sync.aligned;");
+            tc_before_sync();
+            // every A4 row written and every transpose read done: GEMM 4 of sample t
+            if (wg0_sync_or(bad)) {
+                aborted = true;
+                break;
+            }
+            if (ltid == 0) {
+                tc_after_sync();
+                if (t >= 2) bad = !wait_t5(&d4_empty[sl], ((t >> 1) - 1) & 1, budget);
+                if (!bad) {
+                    tc_after_sync();
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) {
+                        const uint32_t d = tmem + kColD4 + 64 * sl + 32 * j;
+                        const uint32_t ah = tmem + kColA4 + 32 * sl + 16 * j, al = ah + 8;
+                        mma_ta(d, ah, dbh, 0);
+                        mma_ta(d, al, dbh, 1);
+                        mma_ta(d, ah, dbl, 1);
+                    }
+                    commit_t5(&d4_full[sl]);
+                }
+            }
+        }
+        if (!aborted && wg0_sync_or(bad)) aborted = true;
+        if (aborted && ltid == 0) atomicExch(a.err, 1);
+    }
+    // every MMA this CTA issued has completed before its tensor memory is freed
+    __syncthreads();
+    if (tid == 0 && tc > 0) {
+        tc_after_sync();
+        commit_t5(&drain);
+        if (!wait_t5(&drain, 0, kWaitCycles)) atomicExch(a.err, 1);
     }
     tc_before_sync();
     __syncthreads();
@@ -318,8 +401,6 @@ __global__ void __launch_bounds__(kT5Threads, 4) tc5_stage_b(Pass p, PassArgs a)
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(kTmemCols));
 }
-
-constexpr size_t kT5Smem = 6 * kTileBytes + 2 * kBBytes;  // A3 hi/lo, A4 hi/lo (2 tiles), B hi/lo
 
 double v16_real(int row, int col) {
     // [[Vr, Vi], [-Vi, Vr]], V[m][k] = exp(-2 pi i m k / 16); rows (re m | im m), cols (re k | im k)
@@ -348,19 +429,23 @@ cudaError_t upload_tc5_tables() {
     return cudaMemcpyToSymbol(g_t5B, B, sizeof B);
 }
 
+int tc5_stage_b_tile() { return kT5Tile; }
+
 cudaError_t tc5_occupancy(int* blocks_per_sm) {
     cudaError_t e = smem_limit_once((const void*)tc5_stage_b, kT5Smem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, tc5_stage_b, kT5Threads, kT5Smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, tc5_stage_b, 2 * kT5Threads, kT5Smem);
+    if (e == cudaSuccess && *blocks_per_sm > 2) *blocks_per_sm = 2;  // tensor memory: 2 x 256 columns
+    return e;
 }
 
 cudaError_t launch_tc5(const Pass& p, const PassArgs& a, cudaStream_t st) {
     if (a.src_kind != SRC_BUF || p.inner % kT5Tile || !a.err) return cudaErrorInvalidValue;
     const int64_t blocks = a.S * (p.inner / kT5Tile);
-    if (blocks <= 0) return cudaSuccess;
+    if (blocks <= 0 || a.tc <= 0) return cudaSuccess;
     cudaError_t e = smem_limit_once((const void*)tc5_stage_b, kT5Smem);
     if (e != cudaSuccess) return e;
-    tc5_stage_b<<<(unsigned)blocks, kT5Threads, kT5Smem, st>>>(p, a);
+    tc5_stage_b<<<(unsigned)blocks, 2 * kT5Threads, kT5Smem, st>>>(p, a);
     return cudaGetLastError();
 }
 

@@ -193,15 +193,34 @@ def correlate_noalloc(levels: Sequence[Level], volts: torch.Tensor, dtype: str,
                       out: torch.Tensor, stream=None) -> torch.Tensor:
     """One integration through omni_correlate_noalloc, which allocates no device
     memory (for callers that cannot allocate; see include/omni.h).  volts:
-    contiguous device [C][T][N][2]; out: contiguous device complex128 [C][Q]."""
-    if not (volts.is_cuda and out.is_cuda and volts.is_contiguous() and out.is_contiguous()):
-        raise ValueError("volts and out must be contiguous CUDA tensors")
+    contiguous device [C][T][N][2] of dtype (int8 for "ci8", float32 or
+    complex64 for "cf32"); out: contiguous device complex128 [C][Q] on the same
+    device.  Every argument is checked here, before the library is called."""
+    if dtype not in DTYPES:
+        raise ValueError(f"dtype must be one of {sorted(DTYPES)}")
+    want = torch.int8 if dtype == "ci8" else torch.float32
+    if volts.dtype == torch.complex64 and dtype == "cf32":
+        volts = torch.view_as_real(volts)
+    if volts.dtype != want:
+        raise TypeError(f"voltages must be {want} [C][T][N][2] for dtype {dtype}, got {volts.dtype}")
+    N, Q = lattice_shape(levels)
+    if volts.dim() != 4 or volts.shape[0] < 1 or volts.shape[2] != N or volts.shape[3] != 2:
+        raise ValueError(f"voltages must have shape [C][T][{N}][2] with C >= 1, got {tuple(volts.shape)}")
+    C, T = int(volts.shape[0]), int(volts.shape[1])
     if out.dtype != torch.complex128:
         raise TypeError("out must be complex128")
-    C, T = int(volts.shape[0]), int(volts.shape[1])
-    _check(load().omni_correlate_noalloc(_levels(levels), len(levels), C, DTYPES[dtype],
-                                         ctypes.c_void_p(volts.data_ptr()), T,
-                                         ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+    if out.numel() != C * Q:
+        raise ValueError(f"out must hold C x Q = {C} x {Q} values, got {out.numel()}")
+    if not (volts.is_contiguous() and out.is_contiguous()):
+        raise ValueError("volts and out must be contiguous")
+    if not (volts.is_cuda and out.is_cuda):
+        raise ValueError("volts and out must be CUDA tensors")
+    if volts.device != out.device:
+        raise ValueError("volts and out must be on the same device")
+    with torch.cuda.device(volts.device):
+        _check(load().omni_correlate_noalloc(_levels(levels), len(levels), C, DTYPES[dtype],
+                                             ctypes.c_void_p(volts.data_ptr()), T,
+                                             ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
     return out
 
 

@@ -199,3 +199,30 @@ def test_fengine_wrapper_rejects_host_tensors():
         omni.fengine(torch.zeros((4, 64), dtype=torch.int8), 8)
     with pytest.raises(ValueError):
         omni.fengine(torch.zeros((4, 64), dtype=torch.int16), 8)
+
+
+def test_noalloc_wrapper_checks_arguments_before_the_library_call(lib):
+    """correlate_noalloc rejects wrong shapes, element types, sizes and devices
+    with ValueError/TypeError before it calls the library (CPU tensors here:
+    every bad case must be caught by the shape and type checks first)."""
+    import torch
+    levels = synth.hierarchy([(4, 4), (2, 3)], [0.0, 0.5], [0.0, 0.1])
+    N, Q = omni.lattice_shape(levels)
+    good_ci8 = torch.zeros((2, 3, N, 2), dtype=torch.int8)
+    out = torch.zeros((2, Q), dtype=torch.complex128)
+    with pytest.raises(TypeError):     # int8 data passed as cf32 would be read 4x past its end
+        omni.correlate_noalloc(levels, good_ci8, "cf32", out)
+    with pytest.raises(TypeError):
+        omni.correlate_noalloc(levels, good_ci8.float(), "ci8", out)
+    with pytest.raises(ValueError):    # wrong antenna count
+        omni.correlate_noalloc(levels, torch.zeros((2, 3, N + 1, 2), dtype=torch.int8), "ci8", out)
+    with pytest.raises(ValueError):    # not [C][T][N][2]
+        omni.correlate_noalloc(levels, torch.zeros((2, 3, N), dtype=torch.int8), "ci8", out)
+    with pytest.raises(ValueError):    # out too small for C x Q
+        omni.correlate_noalloc(levels, good_ci8, "ci8", torch.zeros((1, Q), dtype=torch.complex128))
+    with pytest.raises(TypeError):
+        omni.correlate_noalloc(levels, good_ci8, "ci8", out.real.contiguous())
+    with pytest.raises(ValueError):    # unknown dtype string
+        omni.correlate_noalloc(levels, good_ci8, "cf16", out)
+    with pytest.raises(ValueError):    # host tensors: the last check, still before any launch
+        omni.correlate_noalloc(levels, good_ci8, "ci8", out)
