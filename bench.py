@@ -59,7 +59,15 @@ def parse():
     ap.add_argument("--no-beams", action="store_true", help="skip the beam-space variant")
     ap.add_argument("--no-tiles", action="store_true", help="skip the tile-hybrid variant")
     ap.add_argument("--no-fengine", action="store_true", help="skip the F-engine leg")
+    ap.add_argument("--no-others", action="store_true",
+                    help="skip the other workloads (1-level 16x16, 3-level, 1024x1024, batch of 48)")
     return ap.parse_args()
+
+
+def line_config(w, precision, world):
+    """The `config` of the JSON line: identical for this arm and the reference arm."""
+    return dict(workload_config(w, precision),
+                parallelism=f"{world} ranks x {w.channels} channels" if world > 1 else "single GPU")
 
 
 def workload_config(w, precision):
@@ -255,7 +263,7 @@ def roofline(stats, workload, path_precision, profiled_units=0, serial_shares=No
 
 # ------------------------------------------------------------------ CPU oracle
 
-def oracle_rate(w, x_host, target_s=15.0, max_samples=64):
+def oracle_rate(w, x_host, target_s=15.0, max_samples=64, with_seconds=False):
     """Time the oracle as it stands on channel 0's first samples; antenna-samples/s."""
     from oracle import oracle
     dims = w.dims
@@ -275,7 +283,10 @@ def oracle_rate(w, x_host, target_s=15.0, max_samples=64):
     oracle.correlate(dims, x_host[0:1, 0:ts])
     dt = time.perf_counter() - t0
     units = w.n_antennas * ts
-    return units / dt, cores, f"channel 0, first {ts} samples ({units} antenna-samples), {dt:.1f} s"
+    sample = f"channel 0, first {ts} samples ({units} antenna-samples), {dt:.1f} s"
+    if with_seconds:
+        return units / dt, cores, sample, dt
+    return units / dt, cores, sample
 
 
 # ------------------------------------------------------------------ direct N^2 context
@@ -332,6 +343,9 @@ def synth_indices(w):
 # ------------------------------------------------------------------ arms
 
 def run_reference(args):
+    """The oracle as it stands, timed on this host's cores on a bounded sample of
+    the workload each step (the oracle's cost is exactly linear in samples x
+    channels, so the rate of the sample is the rate of the workload)."""
     from paper_0909_0001_gb300.multirank import rank_env
     rank, _, world = rank_env()
     if rank != 0:
@@ -339,20 +353,27 @@ def run_reference(args):
     from paper_0909_0001_gb300 import synth
     w = synth.workload(args.workload)
     x = synth.voltages(w, channels=1, samples=64)
-    per_step = max(5.0, 150.0 / max(1, args.steps + args.warmup))
+    per_step = max(4.0, 120.0 / max(1, args.steps + args.warmup))
     for _ in range(args.warmup):
         oracle_rate(w, x, target_s=per_step)
-    rates, cores, sample = [], None, ""
+    rates, secs, cores, sample = [], [], None, ""
     for _ in range(args.steps):
-        r, cores, sample = oracle_rate(w, x, target_s=per_step)
+        r, cores, sample, sec = oracle_rate(w, x, target_s=per_step, with_seconds=True)
         rates.append(r)
+        secs.append(sec)
     value = statistics.mean(rates)
-    ms = w.n_antennas * w.samples * w.channels / value * 1e3
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": statistics.mean(secs) * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": workload_config(w, "fp64 oracle"),
+            "config": line_config(w, args.precision, world),
+            "extrapolated": True,
+            "extrapolation": ("each step times the oracle on the bounded sample named in "
+                              "cpu_baseline.sample; ms_per_step is that measured time, and value "
+                              "is the measured rate, which holds for the whole workload because "
+                              "the oracle's cost is linear in samples x channels (full step: "
+                              "%.0f s)" % (w.n_antennas * w.samples * w.channels / value)),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": sample + " per step"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -387,6 +408,126 @@ def timed_steps(plan, x, vis, steps, warmup, stream, barrier, profile):
     return e0.elapsed_time(e1) / steps, plan.kernel_stats(clear=True)
 
 
+PROFILED_STEPS = 2
+
+
+def measure(plan, x, vis, steps, warmup, stream, barrier, units_per_step):
+    """Timed steps with per-launch events off (the number reported), clocks
+    sampled during them; then PROFILED_STEPS more steps with per-launch CUDA
+    events for the kernel shares and the dominant kernel's launch duration.
+    Returns (ms per step, clocks, kernel stats, channel-samples profiled); the
+    stats carry "timed_launches", the launches of the timed (unprofiled) steps."""
+    import torch
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        ms, hstats = timed_steps(plan, x, vis, steps, warmup, stream, barrier, False)
+    _, stats = timed_steps(plan, x, vis, PROFILED_STEPS, 0, stream, lambda: None, True)
+    launches = sum(st["launches"] for st in hstats)
+    for st in stats:
+        st["timed_launches"] = launches
+    return ms, clk.summary(), stats, units_per_step * PROFILED_STEPS
+
+
+def kernel_list(stats):
+    return [{k: s[k] for k in ("name", "launches", "total_ms")} for s in stats if s["launches"]]
+
+
+def other_workloads(args, stream):
+    """The benchmark's other configurations, each timed like the headline and
+    reported as a sub-record: 1-level 16x16 (1 x 64), 3-level (16 x 256),
+    1024x1024 (16 x 64) on every path the library supports for them, and the
+    48 uneven arrays of a batch plan (128 x 512) against 48 separate plans."""
+    import torch
+    from paper_0909_0001_gb300 import omni, synth
+    out = []
+    for name in ("grid16", "hier3", "grid1024"):
+        w = synth.workload(name)
+        x = synth.voltages(w, device="cuda")
+        units = w.n_antennas * w.samples * w.channels
+        rec = {"workload": name, "config": workload_config(w, "see paths"), "paths": {}}
+        for prec in ("mixed", "fp32"):
+            try:
+                plan = omni.Plan(w.levels, w.channels, dtype=w.dtype, precision=prec)
+            except omni.OmniError as e:
+                rec["paths"][prec] = {"unsupported": str(e)}
+                continue
+            vis = torch.empty((w.channels, plan.n_lags), dtype=torch.complex128, device="cuda")
+            steps = max(3, min(args.steps, 10))
+            ms, clocks, stats, prof_units = measure(plan, x, vis, steps, 3, stream, lambda: None,
+                                                    w.channels * w.samples)
+            rec["paths"][prec] = {"value": units / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+                                  "steps": steps, "warmup": 3, "clocks": clocks,
+                                  "roofline": roofline(stats, name, prec, prof_units),
+                                  "kernels": kernel_list(stats)}
+            plan.close()
+            del vis
+        del x
+        torch.cuda.empty_cache()
+        out.append(rec)
+    out.append(batch_record(args, stream))
+    return out
+
+
+def batch_record(args, stream, rank=0, barrier=lambda: None, dev=None):
+    """48 uneven arrays in one batch plan, and the same arrays as 48 plans."""
+    import torch
+    from paper_0909_0001_gb300 import multirank, omni, synth
+    arrays = synth.batch_arrays()
+    C, T = 128, 512
+    volts = synth.batch_voltages(arrays, C, T, device="cuda", seed=9090004 + 1000 * rank)
+    plan = omni.BatchPlan(arrays, C, dtype="ci8")
+    flat = plan.pack(volts)
+    del volts
+    units = plan.n_antennas * C * T
+    vis = torch.empty(C * plan.n_lags, dtype=torch.complex128, device="cuda")
+    steps = max(3, min(args.steps, 10))
+    ms, clocks, stats, prof_units = measure(plan, flat, vis, steps, 3, stream, barrier, C * T)
+    rate, slowest = multirank.job_rate(units, ms * 1e-3, device=dev)
+    singles, offs, off = [], [], 0
+    for levels, N in zip(arrays, plan.antennas):
+        singles.append(omni.Plan(levels, C, dtype="ci8"))
+        offs.append(off)
+        off += C * T * N * 2
+    views = [flat[o:o + C * T * N * 2].view(C, T, N, 2) for o, N in zip(offs, plan.antennas)]
+    outs = [torch.empty((C, q), dtype=torch.complex128, device="cuda") for q in plan.lags]
+
+    def step_all():
+        for sp, v, o in zip(singles, views, outs):
+            sp.correlate(v)
+            sp.visibilities(reset=True, out=o)
+
+    for _ in range(3):
+        step_all()
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step_all()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    sep_ms = e0.elapsed_time(e1) / steps
+    sep_rate, sep_s = multirank.job_rate(units, sep_ms * 1e-3, device=dev)
+    for sp in singles:
+        sp.close()
+    plan.close()
+    del flat, vis, outs
+    torch.cuda.empty_cache()
+    return {"workload": "batch48",
+            "config": {"workload": f"{len(arrays)} uneven arrays (single-level 8x8..64x64, "
+                                   "2-level 4x4 tiles on 8x8/16x16 grids), batch plan",
+                       "arrays": len(arrays), "antennas_total": plan.n_antennas,
+                       "channels": C, "samples": T, "input": "ci8", "precision": "fp32",
+                       "shape_groups": len(set(tuple((l.n1, l.n2) for l in a) for a in arrays)),
+                       "l2": "inputs larger than L2 (%.1f GB per step); no flush"
+                             % (units * 2 / 1e9)},
+            "paths": {"fp32": {"value": rate, "unit": UNIT, "ms_per_step": slowest * 1e3,
+                               "steps": steps, "warmup": 3, "clocks": clocks,
+                               "roofline": roofline(stats, "batch48", "fp32", prof_units),
+                               "kernels": kernel_list(stats),
+                               "separate_plans": {"value": sep_rate, "ms_per_step": sep_s * 1e3,
+                                                  "plans": len(singles)}}}}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -416,14 +557,15 @@ def run_ours(args):
     for prec in precisions:
         plan = omni.Plan(w.levels, w.channels, dtype=w.dtype, precision=prec)
         vis = torch.empty((w.channels, plan.n_lags), dtype=torch.complex128, device="cuda")
-        # both paths are timed the same way: per-pass CUDA events on, clocks sampled
-        with ClockSampler(torch.cuda.current_device()) as clk:
-            ms, stats = timed_steps(plan, x, vis, args.steps, args.warmup, stream, barrier, True)
+        # both paths are timed the same way: per-launch events off, clocks sampled;
+        # then a short second run with per-launch events gives the kernel shares
+        ms, clocks_p, stats, prof_units = measure(plan, x, vis, args.steps, args.warmup, stream,
+                                                  barrier, w.channels * w.samples)
         if prec == args.precision:
-            clocks = clk.summary()
+            clocks = clocks_p
         rate, slowest = multirank.job_rate(units, ms * 1e-3, device=dev)
         results[prec] = {"plan": plan, "vis": vis, "ms": slowest * 1e3, "value": rate,
-                         "stats": stats}
+                         "stats": stats, "prof_units": prof_units, "clocks": clocks_p}
         if prec != args.precision:
             plan.close()
     head = results[args.precision]
@@ -584,6 +726,10 @@ def run_ours(args):
         n2 = {"value": rate_n2, "unit": UNIT, "seconds": sec_n2, "rel_diff_vs_hypercube": diff_n2,
               "sample": f"channel 0, {w.samples} samples, TF32 tensor-core GEMMs + lag binning"}
 
+    others = None
+    if rank == 0 and world == 1 and not args.no_others:
+        others = other_workloads(args, stream)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         r, cores, sample = oracle_rate(w, x[0:1, 0:64].cpu())
@@ -596,17 +742,17 @@ def run_ours(args):
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f16x3+f32" if args.precision == "mixed" else "f32",
                 "data": "synthetic",
-                "config": dict(workload_config(w, args.precision),
-                               parallelism=f"{world} ranks x {w.channels} channels"
-                               if world > 1 else "single GPU"),
-                "roofline": roofline(stats, args.workload, args.precision,
-                                     w.channels * w.samples * args.steps, serial),
+                "config": line_config(w, args.precision, world),
+                "timing": ("ms_per_step and value from CUDA events around the timed steps with "
+                           "per-launch events off; roofline and kernels from %d further steps "
+                           "with per-launch CUDA events" % PROFILED_STEPS),
+                "roofline": roofline(stats, args.workload, args.precision, head["prof_units"],
+                                     serial),
                 "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": sum(s["launches"] for s in stats),
+                "gpu_launches": stats[0]["timed_launches"] if stats else 0,
                 "clocks": clocks, "epilogue": epilogue, "direct_n2": n2, "beam_space": beams,
-                "tile_hybrid": tiles, "fengine": fe,
-                "kernels": [{k: s[k] for k in ("name", "launches", "total_ms")}
-                            for s in stats if s["launches"]]}
+                "tile_hybrid": tiles, "fengine": fe, "other_workloads": others,
+                "kernels": kernel_list(stats)}
         if "fp32" in results and args.precision != "fp32":
             f = results["fp32"]
             line["fp32_path"] = {"value": f["value"], "ms_per_step": f["ms"],
@@ -621,7 +767,7 @@ def run_batch(args):
     """Uneven independent arrays in one batch plan vs one plan per array (FP32 path)."""
     import torch
     import torch.distributed as dist
-    from paper_0909_0001_gb300 import multirank, omni, synth
+    from paper_0909_0001_gb300 import multirank
 
     rank, local_rank, world = multirank.rank_env()
     torch.cuda.set_device(local_rank)
@@ -633,67 +779,16 @@ def run_batch(args):
         if world > 1:
             dist.barrier()
 
-    arrays = synth.batch_arrays()
-    C = args.channels or 128
-    T = args.samples or 512
-    volts = synth.batch_voltages(arrays, C, T, device="cuda", seed=9090004 + 1000 * rank)
-    plan = omni.BatchPlan(arrays, C, dtype="ci8")
-    flat = plan.pack(volts)
-    del volts
-    units = plan.n_antennas * C * T
-    stream = torch.cuda.current_stream()
-    vis = torch.empty(C * plan.n_lags, dtype=torch.complex128, device="cuda")
-    with ClockSampler(torch.cuda.current_device()) as clk:
-        ms, stats = timed_steps(plan, flat, vis, args.steps, args.warmup, stream, barrier, True)
-    rate, slowest = multirank.job_rate(units, ms * 1e-3, device=dev)
-    # the same arrays as separate plans, launched one after another
-    sep = None
-    if not args.no_compare:
-        singles, offs, off = [], [], 0
-        for levels, N in zip(arrays, plan.antennas):
-            singles.append(omni.Plan(levels, C, dtype="ci8"))
-            offs.append(off)
-            off += C * T * N * 2
-        views = [flat[o:o + C * T * N * 2].view(C, T, N, 2) for o, N in zip(offs, plan.antennas)]
-        outs = [torch.empty((C, q), dtype=torch.complex128, device="cuda") for q in plan.lags]
-
-        def step_all():
-            for sp, v, o in zip(singles, views, outs):
-                sp.correlate(v)
-                sp.visibilities(reset=True, out=o)
-
-        for _ in range(max(3, args.warmup)):
-            step_all()
-        barrier()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.steps):
-            step_all()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        sep_ms = e0.elapsed_time(e1) / args.steps
-        sep_rate, sep_s = multirank.job_rate(units, sep_ms * 1e-3, device=dev)
-        sep = {"value": sep_rate, "ms_per_step": sep_s * 1e3, "plans": len(singles)}
-        for sp in singles:
-            sp.close()
+    rec = batch_record(args, torch.cuda.current_stream(), rank=rank, barrier=barrier, dev=dev)
     if rank == 0:
-        line = {"metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": world,
-                "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": slowest * 1e3,
+        f = rec["paths"]["fp32"]
+        line = {"metric": METRIC, "value": f["value"], "unit": UNIT, "n_gpus": world,
+                "steps": f["steps"], "warmup": f["warmup"], "ms_per_step": f["ms_per_step"],
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-                "data": "synthetic",
-                "config": {"workload": f"{len(arrays)} uneven arrays (single-level 8x8..64x64, "
-                                       "2-level 4x4 tiles on 8x8/16x16 grids), batch plan",
-                           "arrays": len(arrays), "antennas_total": plan.n_antennas,
-                           "channels": C, "samples": T, "input": "ci8", "precision": "fp32",
-                           "shape_groups": len(set(tuple((l.n1, l.n2) for l in a) for a in arrays)),
-                           "l2": "inputs larger than L2 (%.1f GB per step); no flush"
-                                 % (flat.numel() / 1e9)},
-                "roofline": roofline(stats, "batch48", "fp32"),
-                "gpu_launches": sum(s["launches"] for s in stats),
-                "clocks": clk.summary(), "separate_plans": sep}
+                "data": "synthetic", "config": rec["config"], "roofline": f["roofline"],
+                "gpu_launches": sum(k["launches"] for k in f["kernels"]) * f["steps"] // PROFILED_STEPS,
+                "clocks": f["clocks"], "separate_plans": f["separate_plans"]}
         print(json.dumps(line), flush=True)
-    plan.close()
     if world > 1:
         dist.destroy_process_group()
 

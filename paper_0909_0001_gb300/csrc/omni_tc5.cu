@@ -44,11 +44,12 @@ constexpr int kBBytes = 4 * kSBO;      // the N = 32, K = 16 B operand
 constexpr uint32_t kTmemCols = 256;    // two CTAs per SM
 constexpr double kT5Fold = 256.0;      // undoes stage A's 1/16 scale, squared
 constexpr float kScale16 = 1.0f / 16.0f;
-// tensor-memory columns
-constexpr uint32_t kColA3 = 0;         // GEMM-3 operand, two slots of 16: hi (8) + lo (8)
-constexpr uint32_t kColD3 = 32;        // GEMM-3 result, 32
-constexpr uint32_t kColA4 = 64;        // GEMM-4 operand, two slots x two row tiles of 16
-constexpr uint32_t kColD4 = 128;       // GEMM-4 result, two slots x two tiles x 32
+// tensor-memory columns (256 per CTA, two CTAs per SM)
+constexpr int kA3Slots = 4;            // GEMM-3 operands prepared ahead of the MMAs
+constexpr uint32_t kColA3 = 0;         // GEMM-3 operand, kA3Slots slots of 16: hi (8) + lo (8)
+constexpr uint32_t kColD3 = 64;        // GEMM-3 result, N = 32
+constexpr uint32_t kColA4 = 96;        // GEMM-4 operand, two row tiles of 16
+constexpr uint32_t kColD4 = 128;       // GEMM-4 result, two row tiles of N = 64
 // transpose buffer [kA_l][k3][m4] float2; rows of one kA_l padded by 16 bytes
 // so that both the writes (lines (kA, m4)) and the reads (lines (kA, k3)) take
 // the minimum number of shared-memory wavefronts
@@ -76,18 +77,24 @@ __device__ __forceinline__ uint64_t sdesc(const void* p) {
            ((uint64_t)(kSBO >> 4) << 32) | ((uint64_t)1 << 46);
 }
 
-// kind::f16, FP32 accumulate, FP16 A and B, K-major, N = 32, M = 128
-constexpr uint32_t kIdesc = (1u << 4) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+// kind::f16, FP32 accumulate, FP16 A and B, K-major, M = 128, N = 32 or 64
+constexpr uint32_t kIdesc32 = (1u << 4) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+constexpr uint32_t kIdesc64 = (1u << 4) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
 
-// D[d] (+)= A[a] . B: A from tensor memory (row = lane, K = 16 FP16 in 8 columns)
-__device__ __forceinline__ void mma_ta(uint32_t d, uint32_t a, uint64_t b, int acc) {
-    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                 " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n"
-                 :: "r"(d), "r"(a), "l"(b), "r"(kIdesc), "r"(acc));
+// D[d] (+)= A[a] . B: A from tensor memory (row = lane, K = 16 FP16 in 8
+// columns).  Executed by a whole warp in uniform control flow with one elected
+// lane issuing: a single divergent thread issuing tcgen05.mma measured ~100
+// cycles per MMA on this part, a warp-uniform elected issue ~30.
+__device__ __forceinline__ void mma_ta(uint32_t d, uint32_t a, uint64_t b, uint32_t idesc, int acc) {
+    asm volatile("{\n .reg .pred p, e;\n setp.ne.b32 p, %4, 0;\n elect.sync _|e, 0xffffffff;\n"
+                 " @e tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n"
+                 :: "r"(d), "r"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
+// Arrive on bar once the warp's earlier MMAs complete (one elected lane commits).
 __device__ __forceinline__ void commit_t5(uint64_t* bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+    asm volatile("{\n .reg .pred e;\n elect.sync _|e, 0xffffffff;\n"
+                 " @e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n}\n"
                  :: "r"(smem_u32(bar)));
 }
 
@@ -121,6 +128,16 @@ __device__ __forceinline__ void ld32(uint32_t taddr, float (&v)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;");
 #pragma unroll
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// tcgen05.ld of 16 columns without the wait (tcgen05.wait::ld before use)
+__device__ __forceinline__ void ld16_async(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                   "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+                   "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                 : "r"(taddr));
 }
 
 __device__ __forceinline__ void st16(uint32_t taddr, const uint32_t (&r)[16]) {
@@ -175,19 +192,23 @@ __device__ __forceinline__ bool wg0_sync_or(bool v) {
     return r != 0;
 }
 
-// Two warpgroups with one tensor-memory lane each per thread (lane = tid % 128):
-// warpgroup 0 turns D3 into the GEMM-4 operand (the transpose) and issues all
-// MMAs; warpgroup 1 loads and splits the voltages' level-1 spectra into the
-// GEMM-3 operand and squares the GEMM-4 results.  They hand off through
-// mbarriers on double-buffered tensor-memory slots (full: written, empty:
-// consumed); GEMM 3 of sample t+1 is issued before the transpose of sample t,
-// so it runs while warpgroup 0 works.
+// Two warpgroups with one tensor-memory lane each per thread (lane = tid % 128).
+// Warpgroup 1 prepares the GEMM-3 operands (level-1 spectra split into FP16
+// hi/lo) up to kA3Slots samples ahead and squares the GEMM-4 results;
+// warpgroup 0 turns D3 into the GEMM-4 operand (the transpose) and its warp 0
+// issues every MMA (warp-uniform, one elected lane).  They hand off through
+// mbarriers (full: written, empty: consumed).  GEMM 3 of sample t+1 is issued
+// before the transpose of sample t, so it runs while warpgroup 0 works.
+// GEMM 3 is three N = 32 products into one accumulator; GEMM 4 is per row tile
+// one N = 64 product of the hi operand with [V16 hi | V16 lo] (the B tables
+// are stored back to back, so the pair is one N = 64 operand) plus one N = 32
+// product of the lo operand with V16 hi, and the squarer adds the two halves.
 __global__ void __launch_bounds__(2 * kT5Threads, 2) tc5_stage_b(Pass p, PassArgs a) {
     extern __shared__ __align__(1024) unsigned char dsm[];
-    unsigned char* bh = dsm;
-    unsigned char* bl = dsm + kBBytes;
+    unsigned char* bh = dsm;               // V16 hi (N = 32); with bl after it, [hi | lo] (N = 64)
+    unsigned char* bl = dsm + kBBytes;     // V16 lo
     unsigned char* xbuf = dsm + 2 * kBBytes;
-    __shared__ __align__(8) uint64_t a3_full[2], a3_empty[2], d3_full, d4_full[2], d4_empty[2];
+    __shared__ __align__(8) uint64_t a3_full[kA3Slots], a3_empty[kA3Slots], d3_full, d4_full, d4_empty;
     __shared__ __align__(8) uint64_t drain, never_bar;  // never_bar: test hook, nothing arrives
     __shared__ uint32_t tmem_slot;
 
@@ -208,13 +229,13 @@ __global__ void __launch_bounds__(2 * kT5Threads, 2) tc5_stage_b(Pass p, PassArg
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < kA3Slots; ++i) {
             mbar_init(&a3_full[i], kT5Threads);
             mbar_init(&a3_empty[i], 1);
-            mbar_init(&d4_full[i], 1);
-            mbar_init(&d4_empty[i], kT5Threads);
         }
         mbar_init(&d3_full, 1);
+        mbar_init(&d4_full, 1);
+        mbar_init(&d4_empty, kT5Threads);
         mbar_init(&drain, 1);
         mbar_init(&never_bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;");
@@ -234,7 +255,7 @@ __global__ void __launch_bounds__(2 * kT5Threads, 2) tc5_stage_b(Pass p, PassArg
     bool aborted = false;
 
     if (wg == 1 && tc > 0) {
-        // ---- warpgroup 1: GEMM-3 operands in, |GEMM-4|^2 out
+        // ---- warpgroup 1: GEMM-3 operands in (ahead), |GEMM-4|^2 out
         // GEMM-3 line (kA_l, m4): Z[8 m4 + m3][kA], m3 = 0..7 (a warp reads two
         // 128-byte runs per m3)
         const float in_scale = p.unscaled_in ? kScale16 : 1.0f;
@@ -245,45 +266,58 @@ __global__ void __launch_bounds__(2 * kT5Threads, 2) tc5_stage_b(Pass p, PassArg
 #pragma unroll
             for (int m3 = 0; m3 < 8; ++m3) pre[m3] = __ldg(b + (int64_t)m3 * p.inner);
         };
+        // operand of sample u (its voltages in pre) into slot u % kA3Slots; the
+        // next sample's spectra are loaded meanwhile
+        auto produce = [&](int u) {
+            const int sl = u % kA3Slots;
+            // warp-uniform verdicts: the tcgen05.st below is .sync.aligned
+            if (u >= kA3Slots &&
+                !__all_sync(0xffffffffu, wait_t5(&a3_empty[sl], (u / kA3Slots - 1) & 1, budget)))
+                return false;
+            uint32_t r[16];
+            split_row(pre, in_scale, r);
+            if (u + 1 < tc) fetch(s0 + u + 1);
+            st16(row + kColA3 + 16 * sl, r);
+            asm volatile("tcgen05.wait::st.sync.aligned;");
+            tc_before_sync();
+            mbar_arrive(&a3_full[sl]);
+            return true;
+        };
         float acc[2][16];
 #pragma unroll
         for (int j = 0; j < 2; ++j)
 #pragma unroll
             for (int k = 0; k < 16; ++k) acc[j][k] = 0.f;
-        auto square = [&](int t) {  // |D4|^2 of sample t, then release its slot
-            const int sl = t & 1;
-            // warp-uniform verdicts: the tcgen05.ld below is .sync.aligned
-            if (!__all_sync(0xffffffffu, wait_t5(&d4_full[sl], (t >> 1) & 1, budget))) return false;
+        auto square = [&](int t) {  // |D4|^2 of sample t, then release D4
+            if (!__all_sync(0xffffffffu, wait_t5(&d4_full, t & 1, budget))) return false;
             tc_after_sync();
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
-                float v[32];
-                ld32(row + kColD4 + 64 * sl + 32 * j, v);
+                uint32_t v[2][16], w[2][16];  // [re, im] of (A_hi + A_lo) . V hi and A_hi . V lo
 #pragma unroll
-                for (int k4 = 0; k4 < 16; ++k4)
-                    acc[j][k4] = fmaf(v[k4], v[k4], fmaf(v[16 + k4], v[16 + k4], acc[j][k4]));
+                for (int part = 0; part < 2; ++part) {
+                    ld16_async(row + kColD4 + 64 * j + 16 * part, v[part]);
+                    ld16_async(row + kColD4 + 64 * j + 32 + 16 * part, w[part]);
+                }
+                asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+                for (int k4 = 0; k4 < 16; ++k4) {
+                    const float re = __uint_as_float(v[0][k4]) + __uint_as_float(w[0][k4]);
+                    const float im = __uint_as_float(v[1][k4]) + __uint_as_float(w[1][k4]);
+                    acc[j][k4] = fmaf(re, re, fmaf(im, im, acc[j][k4]));
+                }
             }
             tc_before_sync();
-            mbar_arrive(&d4_empty[sl]);
+            mbar_arrive(&d4_empty);
             return true;
         };
         fetch(s0);
+        for (int u = 0; u < tc && u < kA3Slots && !aborted; ++u)
+            if (!produce(u)) aborted = true;
         for (int t = 0; t < tc && !aborted; ++t) {
-            const int sl = t & 1;
-            if (t >= 2 && !__all_sync(0xffffffffu, wait_t5(&a3_empty[sl], ((t >> 1) - 1) & 1, budget))) {
-                aborted = true;
-                break;
-            }
-            uint32_t r[16];
-            split_row(pre, in_scale, r);
-            if (t + 1 < tc) fetch(s0 + t + 1);
-            st16(row + kColA3 + 16 * sl, r);
-            asm volatile("tcgen05.wait::st.sync.aligned;");
-            tc_before_sync();
-            mbar_arrive(&a3_full[sl]);
-            if (t >= 1 && !square(t - 1)) aborted = true;
+            if (!square(t)) aborted = true;
+            else if (t + kA3Slots < tc && !produce(t + kA3Slots)) aborted = true;
         }
-        if (!aborted && !square(tc - 1)) aborted = true;
         if (aborted) {
             atomicExch(a.err, 1);
         } else {
@@ -299,19 +333,21 @@ __global__ void __launch_bounds__(2 * kT5Threads, 2) tc5_stage_b(Pass p, PassArg
             }
         }
     } else if (wg == 0 && tc > 0) {
-        // ---- warpgroup 0: D3 -> transpose -> GEMM-4 operand; issues every MMA
+        // ---- warpgroup 0: D3 -> transpose -> GEMM-4 operand; warp 0 issues the MMAs
         const uint64_t dbh = sdesc(bh), dbl = sdesc(bl);
-        auto issue_gemm3 = [&](int sl) {
+        const bool issuer = warp == 0;
+        auto issue_gemm3 = [&](int u) {
+            const int sl = u % kA3Slots;
             const uint32_t d = tmem + kColD3, ah = tmem + kColA3 + 16 * sl, al = ah + 8;
-            mma_ta(d, ah, dbh, 0);
-            mma_ta(d, al, dbh, 1);
-            mma_ta(d, ah, dbl, 1);
+            mma_ta(d, ah, dbh, kIdesc32, 0);
+            mma_ta(d, al, dbh, kIdesc32, 1);
+            mma_ta(d, ah, dbl, kIdesc32, 1);
             commit_t5(&a3_empty[sl]);
             commit_t5(&d3_full);
         };
-        bool bad = false;
-        if (ltid == 0) {
-            bad = !wait_t5(&a3_full[0], 0, budget);
+        bool bad = false;  // warp 0: a wait before an MMA issue expired
+        if (issuer) {
+            bad = !__all_sync(0xffffffffu, wait_t5(&a3_full[0], 0, budget));
             if (!bad) {
                 tc_after_sync();
                 issue_gemm3(0);
@@ -319,10 +355,8 @@ __global__ void __launch_bounds__(2 * kT5Threads, 2) tc5_stage_b(Pass p, PassArg
         }
         aborted = wg0_sync_or(bad);
         float2* xw = reinterpret_cast<float2*>(xbuf + a_kl * kXRow) + a_m4;
-        bad = false;  // thread 0: a wait before an MMA issue expired
         for (int t = 0; t < tc && !aborted; ++t) {
-            const int sl = t & 1;
-            // D3 of sample t (GEMM 4 of sample t-2 is complete too: issued earlier)
+            // D3 of sample t
             const bool ok = (a.force_expire && t == 0) ? wait_t5(&never_bar, 0, kTestWaitCycles)
                                                        : wait_t5(&d3_full, t & 1, budget);
             if (wg0_sync_or(!ok || bad)) {
@@ -332,21 +366,23 @@ __global__ void __launch_bounds__(2 * kT5Threads, 2) tc5_stage_b(Pass p, PassArg
             tc_after_sync();
             float v[32];
             ld32(row + kColD3, v);
-            tc_before_sync();
-            // every D3 row read: GEMM 3 of sample t+1 may overwrite it
-            asm volatile("barrier.cta.sync 1, 128;");
-            if (ltid == 0 && t + 1 < tc) {
-                tc_after_sync();
-                bad = !wait_t5(&a3_full[(t + 1) & 1], ((t + 1) >> 1) & 1, budget);
-                if (!bad) {
-                    tc_after_sync();
-                    issue_gemm3((t + 1) & 1);
-                }
-            }
             // transpose through shared memory: D3 rows (kA_l, m4) -> GEMM-4 rows (kA_l, k3)
 #pragma unroll
             for (int k3 = 0; k3 < 16; ++k3) xw[8 * k3] = make_float2(v[k3], v[16 + k3]);
+            tc_before_sync();
+            // every D3 row read (GEMM 3 of sample t+1 may overwrite it) and every
+            // transpose row written
             asm volatile("barrier.cta.sync 1, 128;");
+            if (issuer && t + 1 < tc) {
+                tc_after_sync();
+                bad = !__all_sync(0xffffffffu,
+                                  wait_t5(&a3_full[(t + 1) % kA3Slots], ((t + 1) / kA3Slots) & 1, budget));
+                if (!bad) {
+                    tc_after_sync();
+                    issue_gemm3(t + 1);
+                }
+            }
+            uint32_t r[2][16];
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
                 const float4* xr = reinterpret_cast<const float4*>(xbuf + kl * kXRow + (8 * j + hi4) * 64);
@@ -357,31 +393,38 @@ __global__ void __launch_bounds__(2 * kT5Threads, 2) tc5_stage_b(Pass p, PassArg
                     z[2 * q] = make_float2(f.x, f.y);
                     z[2 * q + 1] = make_float2(f.z, f.w);
                 }
-                uint32_t r[16];
-                split_row(z, 1.0f, r);
-                st16(row + kColA4 + 32 * sl + 16 * j, r);
+                split_row(z, 1.0f, r[j]);
             }
+            // GEMM 4 of sample t-1 has read A4 (its completion also means D4 is full)
+            const bool ok4 = t == 0 || wait_t5(&d4_full, (t - 1) & 1, budget);
+            if (wg0_sync_or(!ok4)) {
+                aborted = true;
+                break;
+            }
+            tc_after_sync();
+            st16(row + kColA4, r[0]);
+            st16(row + kColA4 + 16, r[1]);
             asm volatile("tcgen05.wait::st.sync.aligned;");
             tc_before_sync();
             // every A4 row written and every transpose read done: GEMM 4 of sample t
+            // once the squarer has read D4 of sample t-1
             if (wg0_sync_or(bad)) {
                 aborted = true;
                 break;
             }
-            if (ltid == 0) {
+            if (issuer) {
                 tc_after_sync();
-                if (t >= 2) bad = !wait_t5(&d4_empty[sl], ((t >> 1) - 1) & 1, budget);
+                if (t >= 1) bad = !__all_sync(0xffffffffu, wait_t5(&d4_empty, (t - 1) & 1, budget));
                 if (!bad) {
                     tc_after_sync();
 #pragma unroll
                     for (int j = 0; j < 2; ++j) {
-                        const uint32_t d = tmem + kColD4 + 64 * sl + 32 * j;
-                        const uint32_t ah = tmem + kColA4 + 32 * sl + 16 * j, al = ah + 8;
-                        mma_ta(d, ah, dbh, 0);
-                        mma_ta(d, al, dbh, 1);
-                        mma_ta(d, ah, dbl, 1);
+                        const uint32_t d = tmem + kColD4 + 64 * j;
+                        const uint32_t ah = tmem + kColA4 + 16 * j, al = ah + 8;
+                        mma_ta(d, ah, dbh, kIdesc64, 0);   // A_hi . [V hi | V lo]
+                        mma_ta(d, al, dbh, kIdesc32, 1);   // + A_lo . V hi
                     }
-                    commit_t5(&d4_full[sl]);
+                    commit_t5(&d4_full);
                 }
             }
         }
@@ -390,10 +433,10 @@ __global__ void __launch_bounds__(2 * kT5Threads, 2) tc5_stage_b(Pass p, PassArg
     }
     // every MMA this CTA issued has completed before its tensor memory is freed
     __syncthreads();
-    if (tid == 0 && tc > 0) {
+    if (warp == 0 && tc > 0) {
         tc_after_sync();
         commit_t5(&drain);
-        if (!wait_t5(&drain, 0, kWaitCycles)) atomicExch(a.err, 1);
+        if (!__all_sync(0xffffffffu, wait_t5(&drain, 0, kWaitCycles)) && tid == 0) atomicExch(a.err, 1);
     }
     tc_before_sync();
     __syncthreads();
