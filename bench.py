@@ -696,28 +696,34 @@ def run_ours(args):
         A2 = np.array(lv2.A, dtype=np.float64).reshape(2, 2)
         grid = np.array([(j1, j2) for j2 in range(lv2.n2) for j1 in range(lv2.n1)], dtype=np.float64)
         offs = grid @ A2.T
-        tp = omni.TilePlan(lv1, offs, w.channels, dtype=w.dtype)
-        tvis = torch.empty((w.channels, tp.n_lags), dtype=torch.complex128, device="cuda")
-        ms_t, tstats = timed_steps(tp, x, tvis, 2, 3, stream, lambda: None, True)
-        # regroup channel 0 by (intra-tile lag, tile-grid lag) and compare
-        Vt = tp.split(tvis)[0]                                   # [i][j][Q1 Q2]
         N1, N2 = lv2.n1, lv2.n2
-        gi = torch.arange(tp.n_tiles, device="cuda")
-        d1 = (gi % N1)[:, None] - (gi % N1)[None, :] + (N1 - 1)
-        d2 = (gi // N1)[:, None] - (gi // N1)[None, :] + (N2 - 1)
-        dg = (d1 + (2 * N1 - 1) * d2).reshape(-1)                    # tile-grid lag index
-        acc = torch.zeros(((2 * N1 - 1) * (2 * N2 - 1), tp.n_tile_lags), dtype=torch.complex128,
-                          device="cuda")
-        acc.index_add_(0, dg, Vt.reshape(-1, tp.n_tile_lags))
-        hyp = vis[0]
-        diff = float((acc.reshape(-1) - hyp).abs().norm() / hyp.abs().norm())
-        tiles = {"value": units / (ms_t * 1e-3), "unit": UNIT, "ms_per_step": ms_t,
-                 "tiles": tp.n_tiles, "pairs": tp.n_tiles ** 2,
-                 "rel_diff_vs_hypercube_ch0": diff,
-                 "kernels": [{k: st[k] for k in ("name", "launches", "total_ms")}
-                             for st in tstats if st["launches"]]}
-        tp.close()
-        del tvis, acc
+        tiles = {"tiles": N1 * N2, "pairs": (N1 * N2) ** 2}
+        for tprec in ("mixed", "fp32"):
+            try:
+                tp = omni.TilePlan(lv1, offs, w.channels, dtype=w.dtype, precision=tprec)
+            except omni.OmniError as e:
+                tiles[tprec] = {"unsupported": str(e)}
+                continue
+            tvis = torch.empty((w.channels, tp.n_lags), dtype=torch.complex128, device="cuda")
+            ms_t, clk_t, tstats, tunits = measure(tp, x, tvis, max(2, min(args.steps, 5)), 3, stream,
+                                                  lambda: None, w.channels * w.samples)
+            # regroup channel 0 by (intra-tile lag, tile-grid lag) and compare
+            Vt = tp.split(tvis)[0]                                   # [i][j][Q1 Q2]
+            gi = torch.arange(tp.n_tiles, device="cuda")
+            d1 = (gi % N1)[:, None] - (gi % N1)[None, :] + (N1 - 1)
+            d2 = (gi // N1)[:, None] - (gi // N1)[None, :] + (N2 - 1)
+            dg = (d1 + (2 * N1 - 1) * d2).reshape(-1)                # tile-grid lag index
+            acc = torch.zeros(((2 * N1 - 1) * (2 * N2 - 1), tp.n_tile_lags), dtype=torch.complex128,
+                              device="cuda")
+            acc.index_add_(0, dg, Vt.reshape(-1, tp.n_tile_lags))
+            hyp = vis[0]
+            diff = float((acc.reshape(-1) - hyp).abs().norm() / hyp.abs().norm())
+            tiles[tprec] = {"value": units / (ms_t * 1e-3), "unit": UNIT, "ms_per_step": ms_t,
+                            "clocks": clk_t, "rel_diff_vs_hypercube_ch0": diff,
+                            "roofline": roofline(tstats, "tiles64", tprec, tunits),
+                            "kernels": kernel_list(tstats)}
+            tp.close()
+            del tvis, acc
 
     n2 = None
     if rank == 0 and not args.no_direct and w.n_antennas <= 16384:

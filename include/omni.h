@@ -148,12 +148,19 @@ omni_status omni_plan_create_beams(const omni_level* levels, int n_levels, int64
  * with N = n_tiles n1 n2, tile slowest; omni_visibilities* write complex128
  * [C][n_tiles][n_tiles][(2 n1 - 1)(2 n2 - 1)], lags dimension 0 fastest.
  * omni_plan_info reports dims (n1, n2, n_tiles, 1) and n_lags = n_tiles^2 Q.
- * The plan's accumulator is [C][n_tiles][n_tiles][4 n1 n2] complex FP64.
- * FP32 path only.  Errors: as omni_plan_create; INVALID_ARG for n_tiles < 1 or
- * a NULL or non-finite offset; UNSUPPORTED beyond 4096 tiles; COLLISION if
- * two antennas of different tiles coincide. */
+ * The plan's accumulator is [C][n_tiles][n_tiles][4 n1 n2] complex FP64
+ * ([C][4 n1 n2][n_tiles][n_tiles] on the mixed path, transposed once per
+ * omni_visibilities call into the plan's scratch before the inverse).
+ * precision OMNI_FP32: the cross-spectra are summed on CUDA cores in FP32;
+ * OMNI_MIXED_FP16: per tile frequency they are one tensor-core GEMM over the
+ * samples (tcgen05, FP16 hi/lo split, FP32 accumulation in tensor memory),
+ * for int8 voltages, at most 64 tiles and 4 n1 n2 a multiple of 4.
+ * Errors: as omni_plan_create; INVALID_ARG for n_tiles < 1 or a NULL or
+ * non-finite offset; UNSUPPORTED beyond 4096 tiles or outside the mixed
+ * path's limits; COLLISION if two antennas of different tiles coincide. */
 omni_status omni_plan_create_tiles(const omni_level* tile, int64_t n_tiles, const double* offsets,
-                                   int64_t n_channels, omni_dtype dtype, omni_plan** out);
+                                   int64_t n_channels, omni_dtype dtype, omni_precision precision,
+                                   omni_plan** out);
 
 /* F-engine (Appendix A, step 2): channelise every antenna's real int8 sample
  * stream into the correlator's input voltages.  Frame t of antenna a, with

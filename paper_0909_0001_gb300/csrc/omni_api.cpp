@@ -371,7 +371,7 @@ omni_status build_passes(omni_plan* pl) {
     }
     pl->fwd.clear();
     pl->fwd_elems = 0;
-    if (pl->precision == OMNI_MIXED_FP16) {
+    if (pl->precision == OMNI_MIXED_FP16 && !pl->n_tiles) {
         // tensor-core stages: level 1 (16x16 -> 32x32 per block), level 2 (8x8 -> 16x16) + |F|^2
         stages.clear();
         Pass pa{};
@@ -438,7 +438,7 @@ omni_status build_passes(omni_plan* pl) {
         // tile hybrid: cross-spectra of every tile pair, per frequency of the tile
         Pass x{};
         x.axis = 0;
-        x.kind = KIND_XSPEC;
+        x.kind = pl->precision == OMNI_MIXED_FP16 ? KIND_XSPEC5 : KIND_XSPEC;
         x.mode = MODE_LAST;
         x.L = g.Lp[0] * g.Lp[1];
         x.n = (int)pl->n_tiles;
@@ -515,6 +515,7 @@ void choose_chunks(omni_plan* pl) {
         case KIND_SMEM: ctas = (last.inner + last.W - 1) / last.W; break;
         case KIND_REG: ctas = (last.inner + 255) / 256; break;
         case KIND_XSPEC: ctas = xspec_ctas_per_channel(last); break;
+        case KIND_XSPEC5: ctas = xspec5_ctas_per_channel(last); break;
         default: ctas = (last.L * last.inner + 255) / 256; break;
     }
     // resident CTA slots of the GPU for that kernel
@@ -526,11 +527,15 @@ void choose_chunks(omni_plan* pl) {
     if (last.kind == KIND_TC_B && tc_occupancy(KIND_TC_B, &per_sm) != cudaSuccess) per_sm = 0;
     if (last.kind == KIND_TC5_B && tc5_occupancy(&per_sm) != cudaSuccess) per_sm = 0;
     if (last.kind == KIND_XSPEC && xspec_occupancy(&per_sm) != cudaSuccess) per_sm = 0;
+    if (last.kind == KIND_XSPEC5 && xspec5_occupancy(&per_sm) != cudaSuccess) per_sm = 0;
     cudaGetLastError();
     int64_t slots = (int64_t)std::max(sms, 1) * std::max(per_sm, 2);
     if (sms <= 0) slots = 304;
     // fill one wave of the last pass: as many channels as the slots hold
     pl->Cc = std::min<int64_t>(pl->C, std::max<int64_t>(1, slots / ctas));
+    // one CTA per SM and a long accumulation per CTA: several waves per chunk
+    // keep the tail small (8 channels: 13.5 waves of 152 for 256 CTAs per channel)
+    if (last.kind == KIND_XSPEC5) pl->Cc = std::min<int64_t>(pl->C, 8);
     if (pl->knobs.chunk_channels > 0) pl->Cc = std::min<int64_t>(pl->C, pl->knobs.chunk_channels);
     const int64_t per_sample = std::max<int64_t>(1, pl->fwd_elems) * (int64_t)sizeof(float2);
     const int64_t samples = std::max<int64_t>(1, target / per_sample);
@@ -538,6 +543,8 @@ void choose_chunks(omni_plan* pl) {
     const int64_t per_chan = std::max<int64_t>(1, pl->inv_elems) * (int64_t)sizeof(float2);
     pl->Cv = std::min<int64_t>(pl->C, std::max<int64_t>(1, target / per_chan));
     pl->buf_elems = std::max(pl->Cc * pl->Tc * pl->fwd_elems, pl->Cv * pl->inv_elems);
+    if (last.kind == KIND_XSPEC5)  // the second buffer also holds the transposed accumulator
+        pl->buf_elems = std::max(pl->buf_elems, pl->Cv * acc_doubles(pl));
 }
 
 // After a stream synchronisation: report (and clear) an expired device wait.
@@ -596,7 +603,7 @@ void release(omni_plan* pl) {
 const char* kind_name(int k) {
     return k == KIND_REG ? "reg" : k == KIND_SMEM ? "smem" : k == KIND_LEVEL ? "level"
          : k == KIND_TC_A || k == KIND_TC_B ? "tc" : k == KIND_TC5_B ? "tcgen05-"
-         : k == KIND_XSPEC ? "xspec" : "direct";
+         : k == KIND_XSPEC ? "xspec" : k == KIND_XSPEC5 ? "xspec-tcgen05-" : "direct";
 }
 const char* mode_name(int m) {
     return m == MODE_MID ? "mid" : m == MODE_LAST ? "last" : m == MODE_INV_MID ? "mid" : "last";
@@ -613,7 +620,8 @@ void init_stats(omni_plan* pl) {
             else
                 snprintf(st.name, sizeof st.name, "%s axis%d %s%d %s", inv ? "inv" : "fwd", p.axis,
                          kind_name(p.kind), p.L, mode_name(p.mode));
-            st.tensor = (p.kind == KIND_TC_A || p.kind == KIND_TC_B || p.kind == KIND_TC5_B) ? 1 : 0;
+            st.tensor = (p.kind == KIND_TC_A || p.kind == KIND_TC_B || p.kind == KIND_TC5_B ||
+                         p.kind == KIND_XSPEC5) ? 1 : 0;
             pl->stats.push_back(st);
         }
     if (pl->split) {  // the FP32 share of a split last pass
@@ -642,7 +650,7 @@ double src_bytes(int src_kind) {
 
 // Algorithmic bytes of one launch: inputs read plus outputs written.
 double pass_bytes(const Pass& p, const PassArgs& a) {
-    if (p.kind == KIND_XSPEC)  // every tile's spectrum once; the FP64 complex fold read and written
+    if (p.kind == KIND_XSPEC || p.kind == KIND_XSPEC5)  // every tile's spectrum once; the FP64 complex fold
         return (double)a.S * a.tc * p.outer * p.L * 8.0 + (double)a.S * p.outer * p.outer * p.L * 32.0;
     const double in = src_bytes(a.src_kind);
     const bool two_axes = p.kind == KIND_LEVEL || p.kind == KIND_TC_A || p.kind == KIND_TC_B ||
@@ -667,6 +675,8 @@ double pass_flops(const Pass& p, const PassArgs& a) {
     switch (p.kind) {
         case KIND_XSPEC:  // one complex multiply-add per tile pair, frequency and sample
             return (double)a.S * a.tc * p.outer * p.outer * p.L * 8.0;
+        case KIND_XSPEC5:  // the same products in real form, FP16 split: 3 x (2 n_tiles)^2 MACs
+            return (double)a.S * a.tc * p.L * 3.0 * (2.0 * p.outer) * (2.0 * p.outer) * 2.0;
         case KIND_TC_A:  // per 16x16 block: 32 + 96 products
             return (double)a.S * p.outer * 128.0 * 4096.0;
         case KIND_TC_B:  // per level-1 frequency and sample: 6 + 12 products, |F|^2
@@ -781,11 +791,22 @@ omni_status check_plan(omni_plan* pl) {
 }
 
 omni_status run_inverse(omni_plan* pl, double2* V, cudaStream_t st) {
+    // mixed tile plans accumulate [K][pair]; transposed to [pair][K] per channel group
+    const bool kmajor = pl->n_tiles && pl->fwd.back().kind == KIND_XSPEC5;
     for (int64_t c0 = 0; c0 < pl->C; c0 += pl->Cv) {
         const int64_t cv = std::min(pl->Cv, pl->C - c0);
         const void* src = pl->P;
         int src_kind = pl->n_tiles ? SRC_PC64 : SRC_P64;
         int64_t src_stride = pl->n_tiles ? acc_doubles(pl) / 2 : pl->g.L;
+        if (kmajor) {
+            const int64_t K = (int64_t)pl->g.Lp[0] * pl->g.Lp[1];
+            cudaError_t e = launch_xspec5_transpose(pl->P + c0 * acc_doubles(pl), acc_doubles(pl), cv, K,
+                                                    pl->n_tiles, pl->buf[1], st);
+            if (e != cudaSuccess) return cuda_fail(e, "accumulator transpose");
+            // the passes index the source by channel c0 + s; the group starts at buf[1]
+            src = reinterpret_cast<const void*>(reinterpret_cast<uintptr_t>(pl->buf[1]) -
+                                                (uintptr_t)(c0 * src_stride * (int64_t)sizeof(double2)));
+        }
         for (size_t k = 0; k < pl->inv.size(); ++k) {
             const Pass& p = pl->inv[k];
             PassArgs a{};
@@ -1176,11 +1197,12 @@ omni_status omni_fengine(const int8_t* raw_dev, int64_t n_antennas, int64_t n_sa
 }
 
 omni_status omni_plan_create_tiles(const omni_level* tile, int64_t n_tiles, const double* offsets,
-                                   int64_t n_channels, omni_dtype dtype, omni_plan** out) {
+                                   int64_t n_channels, omni_dtype dtype, omni_precision precision,
+                                   omni_plan** out) {
     if (n_tiles < 1) return fail(OMNI_ERR_INVALID_ARG, "n_tiles must be >= 1");
     if (!offsets) return fail(OMNI_ERR_INVALID_ARG, "offsets is NULL");
     if (n_tiles > 4096) return fail(OMNI_ERR_UNSUPPORTED, "at most 4096 tiles");
-    return create_plan(tile, 1, n_channels, dtype, OMNI_FP32, knobs_from_env(), out, false, n_tiles, offsets);
+    return create_plan(tile, 1, n_channels, dtype, precision, knobs_from_env(), out, false, n_tiles, offsets);
 }
 
 static omni_status create_plan(const omni_level* levels, int n_levels, int64_t n_channels,
@@ -1197,8 +1219,8 @@ static omni_status create_plan(const omni_level* levels, int n_levels, int64_t n
         return fail(OMNI_ERR_UNSUPPORTED, "beam-space plans run the FP32 path");
     if (beams && levels && n_levels < 2)
         return fail(OMNI_ERR_UNSUPPORTED, "a beam-space plan needs at least two levels");
-    if (n_tiles && precision != OMNI_FP32)
-        return fail(OMNI_ERR_UNSUPPORTED, "tile-hybrid plans run the FP32 path");
+    if (n_tiles && precision == OMNI_MIXED_FP16 && dtype != OMNI_IN_CI8)
+        return fail(OMNI_ERR_UNSUPPORTED, "mixed-precision tile-hybrid plans take int8 voltages");
     omni_plan* pl = new omni_plan();
     pl->beams = beams;
     pl->n_tiles = n_tiles;
@@ -1209,7 +1231,14 @@ static omni_status create_plan(const omni_level* levels, int n_levels, int64_t n
         delete pl;
         return st;
     }
-    if (precision == OMNI_MIXED_FP16 && !tc_supports(pl->g.n, pl->g.D, dtype == OMNI_IN_CI8)) {
+    if (n_tiles && precision == OMNI_MIXED_FP16 &&
+        !xspec5_supports(n_tiles, (int64_t)pl->g.Lp[0] * pl->g.Lp[1])) {
+        delete pl;
+        return fail(OMNI_ERR_UNSUPPORTED,
+                    "mixed-precision tile-hybrid plans support at most 64 tiles whose padded "
+                    "lattice size is a multiple of 4");
+    }
+    if (!n_tiles && precision == OMNI_MIXED_FP16 && !tc_supports(pl->g.n, pl->g.D, dtype == OMNI_IN_CI8)) {
         delete pl;
         return fail(OMNI_ERR_UNSUPPORTED,
                     "the mixed-precision path supports int8 voltages on a 2-level hierarchy of "

@@ -35,7 +35,8 @@ enum PassKind : int {
     KIND_TC_A = 4,   // mixed precision, finest level as split-FP16 tensor-core GEMMs
     KIND_TC_B = 5,   // mixed precision, coarse level + |F|^2 as tensor-core GEMMs (LAST, mma.sync)
     KIND_TC5_B = 6,  // the same on 5th-generation tensor cores (tcgen05, tensor memory)
-    KIND_XSPEC = 7   // tile hybrid: cross-spectra of every tile pair summed over samples (LAST)
+    KIND_XSPEC = 7,  // tile hybrid: cross-spectra of every tile pair summed over samples (LAST)
+    KIND_XSPEC5 = 8  // the same as a tcgen05 GEMM per tile frequency over the samples (mixed precision)
 };
 
 // One axis transform.  The data of one sample (or channel) is viewed as
@@ -113,6 +114,14 @@ cudaError_t launch_tc5(const Pass& p, const PassArgs& a, cudaStream_t stream);
 cudaError_t launch_xspec(const Pass& p, const PassArgs& a, cudaStream_t stream);
 cudaError_t xspec_occupancy(int* blocks_per_sm);
 int64_t xspec_ctas_per_channel(const Pass& p);
+bool xspec5_supports(int64_t n_tiles, int64_t K);  // <= 64 tiles, K a multiple of 4
+cudaError_t launch_xspec5(const Pass& p, const PassArgs& a, cudaStream_t stream);
+cudaError_t xspec5_occupancy(int* blocks_per_sm);
+int64_t xspec5_ctas_per_channel(const Pass& p);
+// The mixed tile plan's accumulator [cv channels from P][K][NT][NT] complex FP64
+// transposed to [NT][NT][K] in dst (the inverse passes' source layout).
+cudaError_t launch_xspec5_transpose(const double* P, int64_t P_stride, int64_t cv, int64_t K, int64_t NT,
+                                    float2* dst, cudaStream_t stream);
 
 // F-engine: frames per antenna, scratch bytes, CTAs of the largest launch, and
 // the launches (fused for F <= 256; else spectra into scratch [N][T][F], then

@@ -1,0 +1,369 @@
+// omni_xspec5.cu -- tile hybrid (Sec. III) between-tile product on 5th-generation
+// tensor cores: the cross-spectra of every tile pair, summed over time, as one
+// GEMM per tile frequency with the samples as the contraction axis.
+//
+// For a tile frequency k let x_t = [Re Y_0..Y_{n-1}(k) | Im Y_0..Y_{n-1}(k)]
+// (n <= 64 tiles, padded with zeros to 128 components) be sample t's synthesized
+// beams.  Then G = sum_t x_t x_t^T (128 x 128, real) holds every cross-spectrum
+//   S_ij(k) = sum_t Y_i(k) conj Y_j(k) = (G[i][j] + G[64+i][64+j]) + i (G[64+i][j] - G[i][64+j]),
+// so the (N/M)^2 term of Sec. III is a real GEMM D[m][n] = sum_t X[m][t] X[n][t]
+// with M = N = 128 and K = the chunk's samples, accumulated in tensor memory.
+// X is split into FP16 hi + lo and each group of 16 samples adds three
+// products, hi.hi^T + hi.lo^T + lo.hi^T (about 22 bits, FP32 accumulation).
+// Scaling: the tile spectra are multiplied by 1/16 before the split (|Y| <=
+// 256 x 127 x sqrt 2 for int8 voltages stays inside FP16) and the FP64 fold
+// multiplies by 256.
+//
+// CTA = (channel of the chunk, 4 consecutive frequencies); 512 tensor-memory
+// columns hold the 4 accumulators, one CTA per SM.  Warps 0-7 are producers:
+// thread (tile j, group of 4 samples) loads the tile's 4 frequencies for 4
+// samples (32-byte runs, the next step's loads in flight while this step is
+// stored), splits them and writes, per frequency and re/im part, half a
+// 16-byte row of the K-major operand tiles of a shared-memory stage.  Warp 8
+// issues the MMAs (warp-uniform, one elected lane) once a stage is full and
+// releases it through an MMA-completion barrier.  At the end warps 0-7 stage
+// each accumulator in shared memory (lane = row) and add S_ij(k) into the FP64
+// complex accumulator, which for this kernel is laid out [k][i][j] so that a
+// CTA's update is one contiguous run; launch_xspec5_transpose turns it into
+// the [i][j][k] layout of the inverse passes once per integration.  Every wait
+// is bounded; on expiry the CTA sets the plan's error word, waits (bounded)
+// for its MMAs, frees its tensor memory and returns.
+#include "omni_fft_common.cuh"
+
+#include <cuda_fp16.h>
+
+#include <cstring>
+
+namespace omni {
+namespace {
+
+constexpr int kXF = 4;            // frequencies per CTA (32-byte load runs)
+constexpr int kXT = 64;           // most tiles (2 x 64 = 128 GEMM rows)
+constexpr int kXThreads = 288;    // warps 0-7 producers / epilogue, warp 8 MMA issue
+constexpr int kXProducers = 256;
+constexpr int kXStages = 3;       // shared-memory operand stages
+constexpr int kLBO = 144;         // bytes between K-adjacent core matrices
+constexpr int kSBO = 272;         // bytes between 8-row groups
+constexpr int kTileBytes = 16 * kSBO;                 // 128 rows x 16 samples, FP16
+constexpr int kStageBytes = kXF * 2 * kTileBytes;     // per frequency: hi, lo
+// more than half of an SM's shared memory: one CTA per SM, so that two CTAs
+// never ask for 512 tensor-memory columns on the same SM
+constexpr size_t kXSmem = (size_t)kXStages * kStageBytes + 1024 > 120 * 1024
+                              ? (size_t)kXStages * kStageBytes + 1024 : 120 * 1024;
+constexpr uint32_t kTmemCols = 512;
+constexpr int kGsPitch = 132;     // floats per row of the epilogue's staging of G (conflict-free)
+constexpr float kXScale = 1.0f / 16.0f;
+constexpr double kXFold = 256.0;
+// kind::f16, FP32 accumulate, FP16 A and B, K-major, M = 128, N = 128
+constexpr uint32_t kIdesc128 = (1u << 4) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+constexpr long long kWaitCycles = 4000000000LL;   // ~2 s
+
+__host__ __device__ inline int tile_off(int row, int k) {
+    return (row >> 3) * kSBO + (k >> 3) * kLBO + (row & 7) * 16 + (k & 7) * 2;
+}
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ uint64_t sdesc(const void* p) {
+    const uint32_t a = smem_u32(p);
+    return (uint64_t)((a >> 4) & 0x3FFF) | ((uint64_t)(kLBO >> 4) << 16) |
+           ((uint64_t)(kSBO >> 4) << 32) | ((uint64_t)1 << 46);
+}
+__device__ __forceinline__ void mma_ss(uint32_t d, uint64_t a, uint64_t b, int acc) {
+    asm volatile("{\n .reg .pred p, e;\n setp.ne.b32 p, %3, 0;\n elect.sync _|e, 0xffffffff;\n"
+                 " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %4, p;\n}\n"
+                 :: "r"(d), "l"(a), "l"(b), "r"(acc), "r"(kIdesc128));
+}
+__device__ __forceinline__ void commit(uint64_t* bar) {
+    asm volatile("{\n .reg .pred e;\n elect.sync _|e, 0xffffffff;\n"
+                 " @e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n}\n"
+                 :: "r"(smem_u32(bar)));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, int count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" :: "r"(smem_u32(bar)));
+}
+__device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, long long budget = kWaitCycles) {
+    const long long t0 = clock64();
+    for (;;) {
+        uint32_t done;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     " selp.u32 %0, 1, 0, p;\n}\n" : "=r"(done) : "r"(smem_u32(bar)), "r"(parity));
+        if (done) return true;
+        if (clock64() - t0 > budget) return false;
+    }
+}
+__device__ __forceinline__ void ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                   "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+                   "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]),
+                   "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+                   "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
+                   "=r"(r[30]), "=r"(r[31])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ uint32_t h2u(__half2 h) {
+    uint32_t u;
+    memcpy(&u, &h, 4);
+    return u;
+}
+// (x0, x1) -> hi = fp16(x), lo = fp16(x - hi), x0 in the low half (the even K element)
+__device__ __forceinline__ void split2(float x0, float x1, uint32_t& hi, uint32_t& lo) {
+    const __half2 h = __floats2half2_rn(x0, x1);
+    const float2 hf = __half22float2(h);
+    hi = h2u(h);
+    lo = h2u(__floats2half2_rn(x0 - hf.x, x1 - hf.y));
+}
+__device__ __forceinline__ void tc_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;"); }
+__device__ __forceinline__ void tc_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;"); }
+
+__global__ void __launch_bounds__(kXThreads, 1) xspec5(Pass p, PassArgs a) {
+    extern __shared__ unsigned char dsm_raw[];
+    // operand stages, 1024-byte aligned
+    unsigned char* dsm = reinterpret_cast<unsigned char*>(((uintptr_t)dsm_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t full[kXStages], empty[kXStages], done;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int abort_flag;
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int NT = (int)p.outer;            // tiles
+    const int64_t K = p.L;                  // tile frequencies
+    const int64_t groups = K / kXF;
+    const int64_t cc = blockIdx.x / groups;
+    const int64_t k0 = (blockIdx.x - cc * groups) * kXF;
+    const int tc = a.tc;
+    const int steps = (tc + 15) / 16;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_u32(&tmem_slot)), "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        for (int i = 0; i < kXStages; ++i) {
+            mbar_init(&full[i], kXProducers);
+            mbar_init(&empty[i], 1);
+        }
+        mbar_init(&done, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    const uint32_t tmem = tmem_slot;
+
+    if (warp < 8) {
+        // ---- producers: thread = (tile j, group g of 4 samples of each 16); the
+        // next step's spectra are loaded while this step's are split and stored
+        const int j = tid & 63, g = tid >> 6;
+        const bool live = j < NT;
+        const float2* Y = reinterpret_cast<const float2*>(a.src);
+        float4 cur[4][2], nxt[4][2];
+        auto fetch = [&](int n, float4 (&y)[4][2]) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int t = 16 * n + 4 * g + q;
+                if (live && t < tc) {
+                    const float4* src = reinterpret_cast<const float4*>(
+                        Y + src_base(a, cc * tc + t) + (int64_t)j * K + k0);
+                    y[q][0] = __ldg(src);
+                    y[q][1] = __ldg(src + 1);
+                } else {
+                    y[q][0] = y[q][1] = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
+        };
+        bool ok = true;
+        if (steps > 0) fetch(0, cur);
+        for (int n = 0; n < steps && ok; ++n) {
+            const int st = n % kXStages;
+            if (n + 1 < steps) fetch(n + 1, nxt);
+            if (n >= kXStages) ok = __all_sync(0xffffffffu, wait_bar(&empty[st], (n / kXStages - 1) & 1));
+            if (!ok) break;
+            unsigned char* stage = dsm + (size_t)st * kStageBytes;
+#pragma unroll
+            for (int f = 0; f < kXF; ++f) {
+                unsigned char* thi = stage + (2 * f) * kTileBytes;
+                unsigned char* tlo = thi + kTileBytes;
+#pragma unroll
+                for (int part = 0; part < 2; ++part) {  // rows j (re) and 64 + j (im)
+                    uint32_t h[2], l[2];
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) {
+                        // frequency f of samples 2q, 2q+1: component 2f + part of the 8 floats
+                        const float4 a0 = cur[2 * q][f >> 1], a1 = cur[2 * q + 1][f >> 1];
+                        const int c = 2 * (f & 1) + part;
+                        const float x0 = (c == 0 ? a0.x : c == 1 ? a0.y : c == 2 ? a0.z : a0.w) * kXScale;
+                        const float x1 = (c == 0 ? a1.x : c == 1 ? a1.y : c == 2 ? a1.z : a1.w) * kXScale;
+                        split2(x0, x1, h[q], l[q]);
+                    }
+                    const int off = tile_off(j + 64 * part, 4 * g);
+                    *reinterpret_cast<uint2*>(thi + off) = make_uint2(h[0], h[1]);
+                    *reinterpret_cast<uint2*>(tlo + off) = make_uint2(l[0], l[1]);
+                }
+            }
+            asm volatile("fence.proxy.async.shared::cta;");
+            mbar_arrive(&full[st]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                cur[q][0] = nxt[q][0];
+                cur[q][1] = nxt[q][1];
+            }
+        }
+        if (!ok) atomicExch(&abort_flag, 1);
+    } else {
+        // ---- warp 8: MMA issue, per stage 3 products per frequency
+        bool ok = true;
+        for (int n = 0; n < steps && ok; ++n) {
+            const int st = n % kXStages;
+            ok = __all_sync(0xffffffffu, wait_bar(&full[st], (n / kXStages) & 1));
+            if (!ok) break;
+            tc_after_sync();
+            unsigned char* stage = dsm + (size_t)st * kStageBytes;
+#pragma unroll
+            for (int f = 0; f < kXF; ++f) {
+                const uint64_t hi = sdesc(stage + (2 * f) * kTileBytes);
+                const uint64_t lo = sdesc(stage + (2 * f + 1) * kTileBytes);
+                const uint32_t d = tmem + 128 * f;
+                mma_ss(d, hi, hi, n > 0);   // hi hi^T
+                mma_ss(d, hi, lo, 1);       // hi lo^T
+                mma_ss(d, lo, hi, 1);       // lo hi^T
+            }
+            commit(&empty[st]);
+        }
+        if (!ok) atomicExch(&abort_flag, 1);
+        commit(&done);  // completion of every MMA issued
+    }
+    __syncthreads();
+    bool fine = abort_flag == 0;
+    if (warp < 8 && fine && steps > 0) {
+        // accumulators complete
+        fine = __all_sync(0xffffffffu, wait_bar(&done, 0));
+    }
+    if (!__syncthreads_and(fine)) {
+        if (tid == 256) atomicExch(a.err, 1);
+        if (warp == 8) wait_bar(&done, 0);  // its MMAs finish before the memory is freed
+    } else if (steps > 0) {
+        tc_after_sync();
+        // epilogue, per frequency: every row of G_f to shared memory (warps w and
+        // w + 4 read the two column halves of lanes 32 (w % 4) ..), then thread
+        // (i parity, j) adds S_ij(k) = (G[i][j] + G[64+i][64+j]) + i (G[64+i][j] -
+        // G[i][64+j]) to the accumulator [k][i][j]: consecutive threads,
+        // consecutive j, so a warp's accesses are 512 contiguous bytes
+        float* gs = reinterpret_cast<float*>(dsm);  // [128][kGsPitch], the stages are free now
+        double2* S = reinterpret_cast<double2*>(a.P + (a.c0 + cc) * a.P_stride);
+        const uint32_t lane_addr = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+        const int r = 32 * (warp & 3) + (tid & 31), half = (warp >> 2) & 1;
+        for (int f = 0; f < kXF; ++f) {
+            if (warp < 8) {
+#pragma unroll
+                for (int c0 = 0; c0 < 64; c0 += 32) {
+                    float v[32];
+                    ld32(lane_addr + 128 * f + 64 * half + c0, v);
+#pragma unroll
+                    for (int q = 0; q < 32; q += 4)
+                        *reinterpret_cast<float4*>(gs + r * kGsPitch + 64 * half + c0 + q) =
+                            make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+                }
+            }
+            __syncthreads();
+            if (warp < 8) {
+                const int jj = tid & 63, ih = tid >> 6;  // i = ih, ih + 4, ...
+                if (jj < NT) {
+                    double2* col = S + ((k0 + f) * (int64_t)NT) * NT + jj;
+                    constexpr int kIB = 16;  // accumulator loads in flight per thread
+                    for (int i0 = ih; i0 < NT; i0 += 4 * kIB) {
+                        double2 cur[kIB];
+#pragma unroll
+                        for (int u = 0; u < kIB; ++u) {
+                            const int i = i0 + 4 * u;
+                            if (i < NT) cur[u] = col[(int64_t)i * NT];
+                        }
+#pragma unroll
+                        for (int u = 0; u < kIB; ++u) {
+                            const int i = i0 + 4 * u;
+                            if (i < NT) {
+                                const float* gi = gs + i * kGsPitch;
+                                const float* gb = gs + (64 + i) * kGsPitch;
+                                cur[u].x += kXFold * ((double)gi[jj] + (double)gb[64 + jj]);
+                                cur[u].y += kXFold * ((double)gb[jj] - (double)gi[64 + jj]);
+                                col[(int64_t)i * NT] = cur[u];
+                            }
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(kTmemCols));
+}
+
+// [K][NT][NT] -> [NT][NT][K] complex FP64 per channel (32 x 32 tiles through
+// shared memory), the layout the tile plan's inverse passes read.
+__global__ void __launch_bounds__(256) xspec5_transpose(const double2* __restrict__ src, int64_t src_stride,
+                                                        double2* __restrict__ dst, int64_t K, int64_t NP) {
+    __shared__ double2 tile[32][33];
+    const int64_t c = blockIdx.z;
+    const int64_t p0 = (int64_t)blockIdx.x * 32, k0 = (int64_t)blockIdx.y * 32;
+    const double2* s = src + c * src_stride;
+    double2* d = dst + c * K * NP;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int r = ty; r < 32; r += 8) {
+        const int64_t k = k0 + r, pp = p0 + tx;
+        if (k < K && pp < NP) tile[r][tx] = s[k * NP + pp];
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+        const int64_t pp = p0 + r, k = k0 + tx;
+        if (k < K && pp < NP) d[pp * K + k] = tile[tx][r];
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_xspec5_transpose(const double* P, int64_t P_stride, int64_t cv, int64_t K, int64_t NT,
+                                    float2* dst, cudaStream_t st) {
+    const int64_t NP = NT * NT;
+    if (cv <= 0) return cudaSuccess;
+    const dim3 grid((unsigned)((NP + 31) / 32), (unsigned)((K + 31) / 32), (unsigned)cv);
+    xspec5_transpose<<<grid, 256, 0, st>>>(reinterpret_cast<const double2*>(P), P_stride / 2,
+                                          reinterpret_cast<double2*>(dst), K, NP);
+    return cudaGetLastError();
+}
+
+bool xspec5_supports(int64_t n_tiles, int64_t K) { return n_tiles >= 1 && n_tiles <= kXT && K % kXF == 0; }
+
+int64_t xspec5_ctas_per_channel(const Pass& p) { return p.L / kXF; }
+
+cudaError_t xspec5_occupancy(int* blocks_per_sm) {
+    cudaError_t e = smem_limit_once((const void*)xspec5, kXSmem);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, xspec5, kXThreads, kXSmem);
+    if (e == cudaSuccess && *blocks_per_sm > 1) *blocks_per_sm = 1;  // 512 tensor-memory columns
+    return e;
+}
+
+cudaError_t launch_xspec5(const Pass& p, const PassArgs& a, cudaStream_t st) {
+    if (a.src_kind != SRC_BUF || !xspec5_supports(p.outer, p.L) || !a.err) return cudaErrorInvalidValue;
+    const int64_t blocks = a.S * xspec5_ctas_per_channel(p);
+    if (blocks <= 0 || a.tc <= 0) return cudaSuccess;
+    cudaError_t e = smem_limit_once((const void*)xspec5, kXSmem);
+    if (e != cudaSuccess) return e;
+    xspec5<<<(unsigned)blocks, kXThreads, kXSmem, st>>>(p, a);
+    return cudaGetLastError();
+}
+
+}  // namespace omni

@@ -74,7 +74,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "omni_plan_create": (ctypes.c_int, [lv, ctypes.c_int, i64, ctypes.c_int, ctypes.c_int,
                                             P(vp)]),
         "omni_plan_create_beams": (ctypes.c_int, [lv, ctypes.c_int, i64, ctypes.c_int, P(vp)]),
-        "omni_plan_create_tiles": (ctypes.c_int, [lv, i64, P(dbl), i64, ctypes.c_int, P(vp)]),
+        "omni_plan_create_tiles": (ctypes.c_int, [lv, i64, P(dbl), i64, ctypes.c_int, ctypes.c_int, P(vp)]),
         "omni_fengine_scratch_bytes": (i64, [i64, i64, i32, i32]),
         "omni_plan_create_tuned": (ctypes.c_int, [lv, ctypes.c_int, i64, ctypes.c_int, ctypes.c_int, vp,
                                                   i64, ctypes.c_char_p, P(ctypes.c_int), P(vp)]),
@@ -456,17 +456,19 @@ class TilePlan(Plan):
     returns [C][n_tiles * n_tiles * Q] complex128; split() views it as
     [C][i][j][Q] (lags of baselines([tile]) order)."""
 
-    def __init__(self, tile: Level, offsets, channels: int, dtype: str = "cf32"):
+    def __init__(self, tile: Level, offsets, channels: int, dtype: str = "cf32",
+                 precision: str = "fp32"):
         self.offsets = np.ascontiguousarray(np.asarray(offsets, dtype=np.float64).reshape(-1, 2))
         self.n_tiles = int(self.offsets.shape[0])
-        super().__init__([tile], channels, dtype=dtype, precision="fp32")
+        super().__init__([tile], channels, dtype=dtype, precision=precision)
         self.n_tile_lags = self.n_lags // (self.n_tiles * self.n_tiles)
 
     def _create(self) -> ctypes.c_void_p:
         h = ctypes.c_void_p()
         off = self.offsets.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         _check(load().omni_plan_create_tiles(_levels(self.levels), self.n_tiles, off,
-                                             self.channels, DTYPES[self.dtype], ctypes.byref(h)))
+                                             self.channels, DTYPES[self.dtype],
+                                             PRECISIONS[self.precision], ctypes.byref(h)))
         return h
 
     def split(self, V: torch.Tensor) -> torch.Tensor:
