@@ -218,6 +218,9 @@ struct Knobs {
     double split_tc = 0.0;        // mixed: share of a chunk's channels on tensor cores, 0 = all (OMNI_SPLIT_TC)
     int tc_stage_a = 1;           // mixed: level 1 on tensor cores (1) or the FP32 FFT (0) (OMNI_TC_STAGE_A;
                                   // measured on the 2-level workload: 20.8 vs 23.9 ms per step)
+    int lag_sum = 1;              // mixed: level 2 as block cross-spectra over time summed by grid
+                                  // offset on tcgen05 (1), or per-sample level-2 DFT-GEMMs (0)
+                                  // (OMNI_MIXED_LAGSUM)
 };
 
 Knobs knobs_from_env() {
@@ -228,6 +231,7 @@ Knobs knobs_from_env() {
     if (const char* e = std::getenv("OMNI_LEVEL_PASSES")) k.level_passes = std::atoi(e) != 0;
     if (const char* e = std::getenv("OMNI_SPLIT_TC")) k.split_tc = std::atof(e);
     if (const char* e = std::getenv("OMNI_TC_STAGE_A")) k.tc_stage_a = std::atoi(e) != 0;
+    if (const char* e = std::getenv("OMNI_MIXED_LAGSUM")) k.lag_sum = std::atoi(e) != 0;
     return k;
 }
 
@@ -242,6 +246,8 @@ struct omni_plan {
     int64_t Cc = 1, Tc = 1;   // forward chunk: channels x samples
     bool beams = false;       // beam-space plan: level-1 axes unpadded, no lag over them
     int64_t n_tiles = 0;      // tile-hybrid plan: identical tiles at arbitrary offsets
+    int64_t lag_pairs = 0;    // mixed 2-level plan with a lag-sum level 2: coarse lags kept per
+                              // level-1 frequency (the accumulator is [L1 L2 of level 1][lag_pairs])
     double inv_scale = 1.0;   // 1 / (points of the inverse transform)
     int64_t Cv = 1;           // inverse batch: channels
     int64_t fwd_elems = 0;    // float2 per sample, largest non-final forward output
@@ -346,6 +352,7 @@ void choose_level(Pass& p) {
 // for a tile-hybrid plan the complex cross-spectra [n_tiles][n_tiles][L1 L2].
 int64_t acc_doubles(const omni_plan* pl) {
     if (pl->n_tiles) return 2 * pl->n_tiles * pl->n_tiles * (int64_t)pl->g.Lp[0] * pl->g.Lp[1];
+    if (pl->lag_pairs) return 2 * pl->lag_pairs * (int64_t)pl->g.Lp[0] * pl->g.Lp[1];
     return pl->g.L;
 }
 
@@ -405,6 +412,21 @@ omni_status build_passes(omni_plan* pl) {
             choose_level(pa);
             pb.unscaled_in = 1;
         }
+        if (pl->knobs.lag_sum) {
+            // level 2 in lag space: per level-1 frequency the 64 x 64 block
+            // cross-spectra summed over the chunk's samples (one tcgen05 GEMM with
+            // the samples as K), then summed over block pairs of equal grid offset
+            pb.kind = KIND_COV5;
+            pb.L = g.Lp[0] * g.Lp[1];
+            pb.n = g.n[2] * g.n[3];
+            pb.outer = (int64_t)g.n[2] * g.n[3];
+            pb.inner = 1;
+            pb.q_out = pb.L;
+            pb.L1 = g.n[2];
+            pb.L2 = g.n[3];
+            pb.W = 0;
+            pl->lag_pairs = (int64_t)(2 * g.n[2] - 1) * (2 * g.n[3] - 1);
+        }
         pl->fwd.push_back(pa);
         pl->fwd.push_back(pb);
         pl->fwd_elems = pa.outer * pa.q_out;
@@ -439,6 +461,7 @@ omni_status build_passes(omni_plan* pl) {
         Pass x{};
         x.axis = 0;
         x.kind = pl->precision == OMNI_MIXED_FP16 ? KIND_XSPEC5 : KIND_XSPEC;
+        x.unscaled_in = 1;  // the tile FFT writes unscaled spectra
         x.mode = MODE_LAST;
         x.L = g.Lp[0] * g.Lp[1];
         x.n = (int)pl->n_tiles;
@@ -453,7 +476,7 @@ omni_status build_passes(omni_plan* pl) {
     pl->inv_elems = 0;
     std::vector<int> inv_axes;
     for (int d : axes)
-        if (!(pl->beams && d < 2)) inv_axes.push_back(d);
+        if (!(pl->beams && d < 2) && !(pl->lag_pairs && d >= 2)) inv_axes.push_back(d);
     if (inv_axes.empty())
         return fail(OMNI_ERR_UNSUPPORTED, "a beam-space plan needs a coarser level with more than one block");
     for (size_t a = inv_axes.size(); a-- > 0;) {
@@ -515,7 +538,8 @@ void choose_chunks(omni_plan* pl) {
         case KIND_SMEM: ctas = (last.inner + last.W - 1) / last.W; break;
         case KIND_REG: ctas = (last.inner + 255) / 256; break;
         case KIND_XSPEC: ctas = xspec_ctas_per_channel(last); break;
-        case KIND_XSPEC5: ctas = xspec5_ctas_per_channel(last); break;
+        case KIND_XSPEC5:
+        case KIND_COV5: ctas = xspec5_ctas_per_channel(last); break;
         default: ctas = (last.L * last.inner + 255) / 256; break;
     }
     // resident CTA slots of the GPU for that kernel
@@ -527,7 +551,8 @@ void choose_chunks(omni_plan* pl) {
     if (last.kind == KIND_TC_B && tc_occupancy(KIND_TC_B, &per_sm) != cudaSuccess) per_sm = 0;
     if (last.kind == KIND_TC5_B && tc5_occupancy(&per_sm) != cudaSuccess) per_sm = 0;
     if (last.kind == KIND_XSPEC && xspec_occupancy(&per_sm) != cudaSuccess) per_sm = 0;
-    if (last.kind == KIND_XSPEC5 && xspec5_occupancy(&per_sm) != cudaSuccess) per_sm = 0;
+    if ((last.kind == KIND_XSPEC5 || last.kind == KIND_COV5) && xspec5_occupancy(&per_sm) != cudaSuccess)
+        per_sm = 0;
     cudaGetLastError();
     int64_t slots = (int64_t)std::max(sms, 1) * std::max(per_sm, 2);
     if (sms <= 0) slots = 304;
@@ -535,7 +560,7 @@ void choose_chunks(omni_plan* pl) {
     pl->Cc = std::min<int64_t>(pl->C, std::max<int64_t>(1, slots / ctas));
     // one CTA per SM and a long accumulation per CTA: several waves per chunk
     // keep the tail small (8 channels: 13.5 waves of 152 for 256 CTAs per channel)
-    if (last.kind == KIND_XSPEC5) pl->Cc = std::min<int64_t>(pl->C, 8);
+    if (last.kind == KIND_XSPEC5 || last.kind == KIND_COV5) pl->Cc = std::min<int64_t>(pl->C, 8);
     if (pl->knobs.chunk_channels > 0) pl->Cc = std::min<int64_t>(pl->C, pl->knobs.chunk_channels);
     const int64_t per_sample = std::max<int64_t>(1, pl->fwd_elems) * (int64_t)sizeof(float2);
     const int64_t samples = std::max<int64_t>(1, target / per_sample);
@@ -543,7 +568,7 @@ void choose_chunks(omni_plan* pl) {
     const int64_t per_chan = std::max<int64_t>(1, pl->inv_elems) * (int64_t)sizeof(float2);
     pl->Cv = std::min<int64_t>(pl->C, std::max<int64_t>(1, target / per_chan));
     pl->buf_elems = std::max(pl->Cc * pl->Tc * pl->fwd_elems, pl->Cv * pl->inv_elems);
-    if (last.kind == KIND_XSPEC5)  // the second buffer also holds the transposed accumulator
+    if (last.kind == KIND_XSPEC5 || last.kind == KIND_COV5)  // the second buffer also holds the transposed accumulator
         pl->buf_elems = std::max(pl->buf_elems, pl->Cv * acc_doubles(pl));
 }
 
@@ -603,7 +628,8 @@ void release(omni_plan* pl) {
 const char* kind_name(int k) {
     return k == KIND_REG ? "reg" : k == KIND_SMEM ? "smem" : k == KIND_LEVEL ? "level"
          : k == KIND_TC_A || k == KIND_TC_B ? "tc" : k == KIND_TC5_B ? "tcgen05-"
-         : k == KIND_XSPEC ? "xspec" : k == KIND_XSPEC5 ? "xspec-tcgen05-" : "direct";
+         : k == KIND_XSPEC ? "xspec" : k == KIND_XSPEC5 ? "xspec-tcgen05-" : k == KIND_COV5 ? "lagsum-tcgen05-"
+         : "direct";
 }
 const char* mode_name(int m) {
     return m == MODE_MID ? "mid" : m == MODE_LAST ? "last" : m == MODE_INV_MID ? "mid" : "last";
@@ -621,7 +647,7 @@ void init_stats(omni_plan* pl) {
                 snprintf(st.name, sizeof st.name, "%s axis%d %s%d %s", inv ? "inv" : "fwd", p.axis,
                          kind_name(p.kind), p.L, mode_name(p.mode));
             st.tensor = (p.kind == KIND_TC_A || p.kind == KIND_TC_B || p.kind == KIND_TC5_B ||
-                         p.kind == KIND_XSPEC5) ? 1 : 0;
+                         p.kind == KIND_XSPEC5 || p.kind == KIND_COV5) ? 1 : 0;
             pl->stats.push_back(st);
         }
     if (pl->split) {  // the FP32 share of a split last pass
@@ -650,6 +676,9 @@ double src_bytes(int src_kind) {
 
 // Algorithmic bytes of one launch: inputs read plus outputs written.
 double pass_bytes(const Pass& p, const PassArgs& a) {
+    if (p.kind == KIND_COV5)  // every block's level-1 spectrum once; the coarse-lag FP64 fold
+        return (double)a.S * a.tc * p.outer * p.L * 8.0 +
+               (double)a.S * p.L * (2.0 * p.L1 - 1) * (2.0 * p.L2 - 1) * 32.0;
     if (p.kind == KIND_XSPEC || p.kind == KIND_XSPEC5)  // every tile's spectrum once; the FP64 complex fold
         return (double)a.S * a.tc * p.outer * p.L * 8.0 + (double)a.S * p.outer * p.outer * p.L * 32.0;
     const double in = src_bytes(a.src_kind);
@@ -675,6 +704,7 @@ double pass_flops(const Pass& p, const PassArgs& a) {
     switch (p.kind) {
         case KIND_XSPEC:  // one complex multiply-add per tile pair, frequency and sample
             return (double)a.S * a.tc * p.outer * p.outer * p.L * 8.0;
+        case KIND_COV5:
         case KIND_XSPEC5:  // the same products in real form, FP16 split: 3 x (2 n_tiles)^2 MACs
             return (double)a.S * a.tc * p.L * 3.0 * (2.0 * p.outer) * (2.0 * p.outer) * 2.0;
         case KIND_TC_A:  // per 16x16 block: 32 + 96 products
@@ -791,17 +821,19 @@ omni_status check_plan(omni_plan* pl) {
 }
 
 omni_status run_inverse(omni_plan* pl, double2* V, cudaStream_t st) {
-    // mixed tile plans accumulate [K][pair]; transposed to [pair][K] per channel group
-    const bool kmajor = pl->n_tiles && pl->fwd.back().kind == KIND_XSPEC5;
+    // mixed tile plans and lag-sum plans accumulate [K][pair]; transposed to
+    // [pair][K] per channel group
+    const bool kmajor = pl->fwd.back().kind == KIND_XSPEC5 || pl->fwd.back().kind == KIND_COV5;
+    const int64_t n_pairs = pl->lag_pairs ? pl->lag_pairs : pl->n_tiles * pl->n_tiles;
     for (int64_t c0 = 0; c0 < pl->C; c0 += pl->Cv) {
         const int64_t cv = std::min(pl->Cv, pl->C - c0);
         const void* src = pl->P;
-        int src_kind = pl->n_tiles ? SRC_PC64 : SRC_P64;
-        int64_t src_stride = pl->n_tiles ? acc_doubles(pl) / 2 : pl->g.L;
+        int src_kind = (pl->n_tiles || pl->lag_pairs) ? SRC_PC64 : SRC_P64;
+        int64_t src_stride = (pl->n_tiles || pl->lag_pairs) ? acc_doubles(pl) / 2 : pl->g.L;
         if (kmajor) {
             const int64_t K = (int64_t)pl->g.Lp[0] * pl->g.Lp[1];
             cudaError_t e = launch_xspec5_transpose(pl->P + c0 * acc_doubles(pl), acc_doubles(pl), cv, K,
-                                                    pl->n_tiles, pl->buf[1], st);
+                                                    n_pairs, pl->buf[1], st);
             if (e != cudaSuccess) return cuda_fail(e, "accumulator transpose");
             // the passes index the source by channel c0 + s; the group starts at buf[1]
             src = reinterpret_cast<const void*>(reinterpret_cast<uintptr_t>(pl->buf[1]) -

@@ -41,7 +41,8 @@ cudaError_t launch_pass(const Pass& p, const PassArgs& a, cudaStream_t st) {
         case KIND_TC_B: return launch_tc(p, a, st);
         case KIND_TC5_B: return launch_tc5(p, a, st);
         case KIND_XSPEC: return launch_xspec(p, a, st);
-        case KIND_XSPEC5: return launch_xspec5(p, a, st);
+        case KIND_XSPEC5:
+        case KIND_COV5: return launch_xspec5(p, a, st);
         default: return launch_direct(p, a, st);
     }
 }

@@ -36,7 +36,9 @@ enum PassKind : int {
     KIND_TC_B = 5,   // mixed precision, coarse level + |F|^2 as tensor-core GEMMs (LAST, mma.sync)
     KIND_TC5_B = 6,  // the same on 5th-generation tensor cores (tcgen05, tensor memory)
     KIND_XSPEC = 7,  // tile hybrid: cross-spectra of every tile pair summed over samples (LAST)
-    KIND_XSPEC5 = 8  // the same as a tcgen05 GEMM per tile frequency over the samples (mixed precision)
+    KIND_XSPEC5 = 8, // the same as a tcgen05 GEMM per tile frequency over the samples (mixed precision)
+    KIND_COV5 = 9    // 2-level mixed path: block cross-spectra per level-1 frequency (tcgen05 GEMM over
+                     // the samples) summed by level-2 grid offset (LAST; L1 x L2 = the level-2 shape)
 };
 
 // One axis transform.  The data of one sample (or channel) is viewed as
@@ -118,9 +120,9 @@ bool xspec5_supports(int64_t n_tiles, int64_t K);  // <= 64 tiles, K a multiple 
 cudaError_t launch_xspec5(const Pass& p, const PassArgs& a, cudaStream_t stream);
 cudaError_t xspec5_occupancy(int* blocks_per_sm);
 int64_t xspec5_ctas_per_channel(const Pass& p);
-// The mixed tile plan's accumulator [cv channels from P][K][NT][NT] complex FP64
-// transposed to [NT][NT][K] in dst (the inverse passes' source layout).
-cudaError_t launch_xspec5_transpose(const double* P, int64_t P_stride, int64_t cv, int64_t K, int64_t NT,
+// An accumulator [cv channels from P][K][NP] complex FP64 (NP tile pairs or
+// coarse lags) transposed to [NP][K] in dst (the inverse passes' source layout).
+cudaError_t launch_xspec5_transpose(const double* P, int64_t P_stride, int64_t cv, int64_t K, int64_t NP,
                                     float2* dst, cudaStream_t stream);
 
 // F-engine: frames per antenna, scratch bytes, CTAs of the largest launch, and

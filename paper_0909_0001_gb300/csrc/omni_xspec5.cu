@@ -30,26 +30,33 @@
 // for its MMAs, frees its tensor memory and returns.
 #include "omni_fft_common.cuh"
 
+#include <cuda.h>            // CUtensorMap; the encoder is fetched from the driver at run time
 #include <cuda_fp16.h>
+#include <cudaTypedefs.h>
 
 #include <cstring>
+#include <mutex>
 
 namespace omni {
 namespace {
 
 constexpr int kXF = 4;            // frequencies per CTA (32-byte load runs)
 constexpr int kXT = 64;           // most tiles (2 x 64 = 128 GEMM rows)
-constexpr int kXThreads = 288;    // warps 0-7 producers / epilogue, warp 8 MMA issue
+constexpr int kXThreads = 320;    // warps 0-7 convert / epilogue, warp 8 MMA issue, warp 9 TMA
 constexpr int kXProducers = 256;
 constexpr int kXStages = 3;       // shared-memory operand stages
 constexpr int kLBO = 144;         // bytes between K-adjacent core matrices
 constexpr int kSBO = 272;         // bytes between 8-row groups
 constexpr int kTileBytes = 16 * kSBO;                 // 128 rows x 16 samples, FP16
 constexpr int kStageBytes = kXF * 2 * kTileBytes;     // per frequency: hi, lo
-// more than half of an SM's shared memory: one CTA per SM, so that two CTAs
-// never ask for 512 tensor-memory columns on the same SM
-constexpr size_t kXSmem = (size_t)kXStages * kStageBytes + 1024 > 120 * 1024
-                              ? (size_t)kXStages * kStageBytes + 1024 : 120 * 1024;
+// raw spectra brought in by the tensor-memory-access unit, kXRaw steps in
+// flight: one box [sample 16][tile < 64][4 frequencies x (re, im) FP32] per step
+constexpr int kXRaw = 3;
+constexpr int kRawBytes = 16 * 64 * 32;
+// more than half of an SM's shared memory (one CTA per SM, so that two CTAs
+// never ask for 512 tensor-memory columns on the same SM)
+constexpr size_t kXSmem = (size_t)kXStages * kStageBytes + (size_t)kXRaw * kRawBytes + 1024;
+static_assert(kXSmem > 114 * 1024 && kXSmem <= 227 * 1024, "one CTA per SM");
 constexpr uint32_t kTmemCols = 512;
 constexpr int kGsPitch = 132;     // floats per row of the epilogue's staging of G (conflict-free)
 constexpr float kXScale = 1.0f / 16.0f;
@@ -121,14 +128,39 @@ __device__ __forceinline__ void split2(float x0, float x1, uint32_t& hi, uint32_
     hi = h2u(h);
     lo = h2u(__floats2half2_rn(x0 - hf.x, x1 - hf.y));
 }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(smem_u32(bar)), "r"(bytes));
+}
+// One box of the 3-D tensor map into shared memory, completing on bar.
+__device__ __forceinline__ void tma_load3(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
+    asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+                 " [%0], [%1, {%2, %3, %4}], [%5];"
+                 :: "r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z),
+                    "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ bool elect_one() {
+    uint32_t e;
+    asm volatile("{\n .reg .pred p;\n elect.sync _|p, 0xffffffff;\n selp.u32 %0, 1, 0, p;\n}\n" : "=r"(e));
+    return e != 0;
+}
 __device__ __forceinline__ void tc_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;"); }
 __device__ __forceinline__ void tc_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;"); }
 
-__global__ void __launch_bounds__(kXThreads, 1) xspec5(Pass p, PassArgs a) {
+// EPI_PAIRS: add every S_ij(k) to the accumulator [k][i][j] (tile hybrid).
+// EPI_LAGS: the tiles are the n3 x n4 blocks of a 2-level hierarchy (index
+// m3 + n3 m4) and only the sums of S_ij over block pairs with equal grid
+// offset (d3, d4) = g(i) - g(j) are kept, in the accumulator [k][q2] with
+// q2 = (d3 + n3 - 1) + (2 n3 - 1)(d4 + n4 - 1): the coarse level's
+// correlation (Eq. ProofEq2 over the level-2 axes) done in lag space.
+enum { EPI_PAIRS = 0, EPI_LAGS = 1 };
+
+template <int EPI>
+__global__ void __launch_bounds__(kXThreads, 1) xspec5(Pass p, PassArgs a, const __grid_constant__ CUtensorMap tmap) {
     extern __shared__ unsigned char dsm_raw[];
     // operand stages, 1024-byte aligned
     unsigned char* dsm = reinterpret_cast<unsigned char*>(((uintptr_t)dsm_raw + 1023) & ~(uintptr_t)1023);
-    __shared__ __align__(8) uint64_t full[kXStages], empty[kXStages], done;
+    __shared__ __align__(8) uint64_t full[kXStages], empty[kXStages], done, raw_full[kXRaw], raw_empty[kXRaw];
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
 
@@ -152,6 +184,10 @@ __global__ void __launch_bounds__(kXThreads, 1) xspec5(Pass p, PassArgs a) {
             mbar_init(&empty[i], 1);
         }
         mbar_init(&done, 1);
+        for (int i = 0; i < kXRaw; ++i) {
+            mbar_init(&raw_full[i], 1);
+            mbar_init(&raw_empty[i], kXProducers);
+        }
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
@@ -161,31 +197,34 @@ __global__ void __launch_bounds__(kXThreads, 1) xspec5(Pass p, PassArgs a) {
     const uint32_t tmem = tmem_slot;
 
     if (warp < 8) {
-        // ---- producers: thread = (tile j, group g of 4 samples of each 16); the
-        // next step's spectra are loaded while this step's are split and stored
+        // ---- converters: thread = (tile j, group g of 4 samples of each 16) takes
+        // its 4 x 32 bytes of the step's raw box, splits them into FP16 hi/lo and
+        // writes the operand tiles; samples past the chunk's end (the box runs on
+        // into the next channel) count as zero
         const int j = tid & 63, g = tid >> 6;
         const bool live = j < NT;
-        const float2* Y = reinterpret_cast<const float2*>(a.src);
-        float4 cur[4][2], nxt[4][2];
-        auto fetch = [&](int n, float4 (&y)[4][2]) {
+        // spectra from the FP32 tile FFT get the 1/16 here; the tensor-core first
+        // pass of a hierarchy already wrote them scaled
+        const float in_scale = p.unscaled_in ? kXScale : 1.0f;
+        const unsigned char* raw = dsm + (size_t)kXStages * kStageBytes;
+        bool ok = true;
+        for (int n = 0; n < steps && ok; ++n) {
+            const int st = n % kXStages, rs = n % kXRaw;
+            ok = __all_sync(0xffffffffu, wait_bar(&raw_full[rs], (n / kXRaw) & 1));
+            if (!ok) break;
+            float4 cur[4][2];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int t = 16 * n + 4 * g + q;
                 if (live && t < tc) {
-                    const float4* src = reinterpret_cast<const float4*>(
-                        Y + src_base(a, cc * tc + t) + (int64_t)j * K + k0);
-                    y[q][0] = __ldg(src);
-                    y[q][1] = __ldg(src + 1);
+                    const float4* r = reinterpret_cast<const float4*>(
+                        raw + (size_t)rs * kRawBytes + ((4 * g + q) * NT + j) * 32);
+                    cur[q][0] = r[0];
+                    cur[q][1] = r[1];
                 } else {
-                    y[q][0] = y[q][1] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    cur[q][0] = cur[q][1] = make_float4(0.f, 0.f, 0.f, 0.f);
                 }
             }
-        };
-        bool ok = true;
-        if (steps > 0) fetch(0, cur);
-        for (int n = 0; n < steps && ok; ++n) {
-            const int st = n % kXStages;
-            if (n + 1 < steps) fetch(n + 1, nxt);
             if (n >= kXStages) ok = __all_sync(0xffffffffu, wait_bar(&empty[st], (n / kXStages - 1) & 1));
             if (!ok) break;
             unsigned char* stage = dsm + (size_t)st * kStageBytes;
@@ -201,8 +240,8 @@ __global__ void __launch_bounds__(kXThreads, 1) xspec5(Pass p, PassArgs a) {
                         // frequency f of samples 2q, 2q+1: component 2f + part of the 8 floats
                         const float4 a0 = cur[2 * q][f >> 1], a1 = cur[2 * q + 1][f >> 1];
                         const int c = 2 * (f & 1) + part;
-                        const float x0 = (c == 0 ? a0.x : c == 1 ? a0.y : c == 2 ? a0.z : a0.w) * kXScale;
-                        const float x1 = (c == 0 ? a1.x : c == 1 ? a1.y : c == 2 ? a1.z : a1.w) * kXScale;
+                        const float x0 = (c == 0 ? a0.x : c == 1 ? a0.y : c == 2 ? a0.z : a0.w) * in_scale;
+                        const float x1 = (c == 0 ? a1.x : c == 1 ? a1.y : c == 2 ? a1.z : a1.w) * in_scale;
                         split2(x0, x1, h[q], l[q]);
                     }
                     const int off = tile_off(j + 64 * part, 4 * g);
@@ -210,15 +249,37 @@ __global__ void __launch_bounds__(kXThreads, 1) xspec5(Pass p, PassArgs a) {
                     *reinterpret_cast<uint2*>(tlo + off) = make_uint2(l[0], l[1]);
                 }
             }
+            // the raw values have been consumed (split and stored) and the operand
+            // stores are ordered before the MMAs' and the next box's asynchronous
+            // accesses: release both
             asm volatile("fence.proxy.async.shared::cta;");
             mbar_arrive(&full[st]);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                cur[q][0] = nxt[q][0];
-                cur[q][1] = nxt[q][1];
-            }
+            mbar_arrive(&raw_empty[rs]);
         }
         if (!ok) atomicExch(&abort_flag, 1);
+    } else if (warp == 9) {
+        // ---- warp 9: the tensor-memory-access loads, kXRaw steps ahead; box
+        // (x = 8 floats from frequency k0, y = every tile, z = 16 samples)
+        bool ok = true;
+        const uint32_t box_bytes = (uint32_t)(16 * NT * 32);
+        int issued = 0;
+        for (int n = 0; n < steps && ok; ++n) {
+            const int rs = n % kXRaw;
+            if (n >= kXRaw) ok = __all_sync(0xffffffffu, wait_bar(&raw_empty[rs], (n / kXRaw - 1) & 1));
+            if (!ok) break;
+            if (elect_one()) {
+                mbar_expect_tx(&raw_full[rs], box_bytes);
+                tma_load3(dsm + (size_t)kXStages * kStageBytes + (size_t)rs * kRawBytes, &tmap, (int)(2 * k0), 0,
+                          (int)(cc * tc + 16 * n), &raw_full[rs]);
+            }
+            __syncwarp();
+            issued = n + 1;
+        }
+        // every box issued has landed before the CTA can leave (bounded; on the
+        // normal path the converters already waited for each of them)
+        for (int n = issued > kXRaw ? issued - kXRaw : 0; n < issued; ++n)
+            if (!wait_bar(&raw_full[n % kXRaw], (n / kXRaw) & 1)) ok = false;
+        if (!__all_sync(0xffffffffu, ok)) atomicExch(&abort_flag, 1);
     } else {
         // ---- warp 8: MMA issue, per stage 3 products per frequency
         bool ok = true;
@@ -275,7 +336,7 @@ __global__ void __launch_bounds__(kXThreads, 1) xspec5(Pass p, PassArgs a) {
                 }
             }
             __syncthreads();
-            if (warp < 8) {
+            if (EPI == EPI_PAIRS && warp < 8) {
                 const int jj = tid & 63, ih = tid >> 6;  // i = ih, ih + 4, ...
                 if (jj < NT) {
                     double2* col = S + ((k0 + f) * (int64_t)NT) * NT + jj;
@@ -301,6 +362,25 @@ __global__ void __launch_bounds__(kXThreads, 1) xspec5(Pass p, PassArgs a) {
                     }
                 }
             }
+            if (EPI == EPI_LAGS && warp < 8) {
+                // q2 per thread: the sum of S_ij over the block pairs of one grid offset
+                const int n3 = p.L1, n4 = p.L2, w3 = 2 * n3 - 1, Q2 = w3 * (2 * n4 - 1);
+                for (int q2 = tid; q2 < Q2; q2 += kXProducers) {
+                    const int d3 = q2 % w3 - (n3 - 1), d4 = q2 / w3 - (n4 - 1);
+                    float re = 0.f, im = 0.f;
+                    for (int m4 = max(0, -d4); m4 < min(n4, n4 - d4); ++m4)
+                        for (int m3 = max(0, -d3); m3 < min(n3, n3 - d3); ++m3) {
+                            const int jb = m3 + n3 * m4, ib = jb + d3 + n3 * d4;
+                            const float* gi = gs + ib * kGsPitch;
+                            const float* gb = gs + (64 + ib) * kGsPitch;
+                            re += gi[jb] + gb[64 + jb];
+                            im += gb[jb] - gi[64 + jb];
+                        }
+                    double2& r = S[(k0 + f) * (int64_t)Q2 + q2];
+                    r.x += kXFold * (double)re;
+                    r.y += kXFold * (double)im;
+                }
+            }
             __syncthreads();
         }
     }
@@ -311,8 +391,8 @@ __global__ void __launch_bounds__(kXThreads, 1) xspec5(Pass p, PassArgs a) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(kTmemCols));
 }
 
-// [K][NT][NT] -> [NT][NT][K] complex FP64 per channel (32 x 32 tiles through
-// shared memory), the layout the tile plan's inverse passes read.
+// [K][NP] -> [NP][K] complex FP64 per channel (32 x 32 tiles through shared
+// memory), the layout the inverse passes read; NP = tile pairs or coarse lags.
 __global__ void __launch_bounds__(256) xspec5_transpose(const double2* __restrict__ src, int64_t src_stride,
                                                         double2* __restrict__ dst, int64_t K, int64_t NP) {
     __shared__ double2 tile[32][33];
@@ -334,9 +414,8 @@ __global__ void __launch_bounds__(256) xspec5_transpose(const double2* __restric
 
 }  // namespace
 
-cudaError_t launch_xspec5_transpose(const double* P, int64_t P_stride, int64_t cv, int64_t K, int64_t NT,
+cudaError_t launch_xspec5_transpose(const double* P, int64_t P_stride, int64_t cv, int64_t K, int64_t NP,
                                     float2* dst, cudaStream_t st) {
-    const int64_t NP = NT * NT;
     if (cv <= 0) return cudaSuccess;
     const dim3 grid((unsigned)((NP + 31) / 32), (unsigned)((K + 31) / 32), (unsigned)cv);
     xspec5_transpose<<<grid, 256, 0, st>>>(reinterpret_cast<const double2*>(P), P_stride / 2,
@@ -349,20 +428,55 @@ bool xspec5_supports(int64_t n_tiles, int64_t K) { return n_tiles >= 1 && n_tile
 int64_t xspec5_ctas_per_channel(const Pass& p) { return p.L / kXF; }
 
 cudaError_t xspec5_occupancy(int* blocks_per_sm) {
-    cudaError_t e = smem_limit_once((const void*)xspec5, kXSmem);
+    cudaError_t e = smem_limit_once((const void*)xspec5<EPI_PAIRS>, kXSmem);
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, xspec5, kXThreads, kXSmem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, xspec5<EPI_PAIRS>, kXThreads, kXSmem);
     if (e == cudaSuccess && *blocks_per_sm > 1) *blocks_per_sm = 1;  // 512 tensor-memory columns
     return e;
+}
+
+// 3-D map of the spectra [samples][tiles][2K floats] for the box of one step.
+static cudaError_t encode_map(const PassArgs& a, const Pass& p, CUtensorMap* map) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    });
+    if (!encode) return cudaErrorNotSupported;
+    const cuuint64_t K = (cuuint64_t)p.L, NT = (cuuint64_t)p.outer;
+    const cuuint64_t dims[3] = {2 * K, NT, (cuuint64_t)(a.S * a.tc)};
+    const cuuint64_t strides[2] = {K * 8, NT * K * 8};
+    const cuuint32_t box[3] = {8, (cuuint32_t)NT, 16};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(a.src), dims, strides, box,
+                              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 cudaError_t launch_xspec5(const Pass& p, const PassArgs& a, cudaStream_t st) {
     if (a.src_kind != SRC_BUF || !xspec5_supports(p.outer, p.L) || !a.err) return cudaErrorInvalidValue;
     const int64_t blocks = a.S * xspec5_ctas_per_channel(p);
     if (blocks <= 0 || a.tc <= 0) return cudaSuccess;
-    cudaError_t e = smem_limit_once((const void*)xspec5, kXSmem);
+    // the TMA unit wants a 16-byte aligned base and row pitches
+    if (reinterpret_cast<uintptr_t>(a.src) % 16 || (p.L * 8) % 16) return cudaErrorInvalidValue;
+    CUtensorMap map;
+    cudaError_t me = encode_map(a, p, &map);
+    if (me != cudaSuccess) return me;
+    if (p.kind == KIND_COV5) {
+        if (p.L1 < 1 || p.L2 < 1 || p.L1 * p.L2 != p.outer) return cudaErrorInvalidValue;
+        cudaError_t e = smem_limit_once((const void*)xspec5<EPI_LAGS>, kXSmem);
+        if (e != cudaSuccess) return e;
+        xspec5<EPI_LAGS><<<(unsigned)blocks, kXThreads, kXSmem, st>>>(p, a, map);
+        return cudaGetLastError();
+    }
+    cudaError_t e = smem_limit_once((const void*)xspec5<EPI_PAIRS>, kXSmem);
     if (e != cudaSuccess) return e;
-    xspec5<<<(unsigned)blocks, kXThreads, kXSmem, st>>>(p, a);
+    xspec5<EPI_PAIRS><<<(unsigned)blocks, kXThreads, kXSmem, st>>>(p, a, map);
     return cudaGetLastError();
 }
 

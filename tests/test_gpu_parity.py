@@ -306,13 +306,36 @@ def test_mixed_rejects_unsupported_shapes():
 
 
 def test_mixed_tcgen05_variant(monkeypatch):
-    """The tensor-memory (tcgen05) stage B gives the same visibilities."""
+    """The tensor-memory (tcgen05) form of the per-sample level-2 DFT-GEMMs gives
+    the same visibilities as the mma.sync form."""
     w = synth.workload("hier2")
     x = synth.voltages(w, channels=2, samples=9)
+    monkeypatch.setenv("OMNI_MIXED_LAGSUM", "0")
     default = gpu_vis(w.levels, x, dtype="ci8", precision="mixed")
     monkeypatch.setenv("OMNI_TCGEN05", "1")
     V, _ = check(w.levels, x, dtype="ci8", tol=TOL_MIXED, precision="mixed")
     assert relerr_per_channel(V, default) <= 1e-6
+
+
+@pytest.mark.parametrize("lagsum", ["1", "0"])
+def test_mixed_level2_forms_agree(monkeypatch, lagsum):
+    """Level 2 in lag space (block cross-spectra over time as a tcgen05 GEMM,
+    summed by grid offset) and as per-sample DFT-GEMMs: each within the mixed
+    bar of the oracle and of each other; sample counts off the 16-sample step."""
+    w = synth.workload("hier2")
+    x = synth.voltages(w, channels=3, samples=37)
+    monkeypatch.setenv("OMNI_MIXED_LAGSUM", lagsum)
+    V, _ = check(w.levels, x, dtype="ci8", tol=TOL_MIXED, precision="mixed")
+    monkeypatch.setenv("OMNI_MIXED_LAGSUM", "0" if lagsum == "1" else "1")
+    other = gpu_vis(w.levels, x, dtype="ci8", precision="mixed")
+    assert relerr_per_channel(V, other) <= 2e-5
+
+
+def test_mixed_lagsum_many_steps():
+    """100 samples: seven 16-sample steps, more than the lag-sum kernel's rings."""
+    w = synth.workload("hier2")
+    x = synth.voltages(w, channels=2, samples=100)
+    check(w.levels, x, dtype="ci8", tol=TOL_MIXED, precision="mixed")
 
 
 @pytest.mark.parametrize("stage_a", ["0", "1"])
@@ -333,6 +356,7 @@ def test_mixed_split_last_pass(monkeypatch, frac):
     (run concurrently) give the same visibilities as either alone."""
     w = synth.workload("hier2")
     x = synth.voltages(w, channels=11, samples=6)
+    monkeypatch.setenv("OMNI_MIXED_LAGSUM", "0")
     monkeypatch.setenv("OMNI_SPLIT_TC", "0")
     tc_only = gpu_vis(w.levels, x, dtype="ci8", precision="mixed")
     monkeypatch.setenv("OMNI_SPLIT_TC", frac)
@@ -351,6 +375,7 @@ def test_expired_tensor_core_wait_is_reported(monkeypatch):
     with a budget of ~0.5 ms, so nothing hangs or faults."""
     w = synth.workload("hier2")
     x = synth.voltages(w, channels=1, samples=3).cuda()
+    monkeypatch.setenv("OMNI_MIXED_LAGSUM", "0")
     monkeypatch.setenv("OMNI_TCGEN05", "1")
     monkeypatch.setenv("OMNI_TEST_FORCE_TIMEOUT", "1")
     with omni.Plan(w.levels, 1, dtype="ci8", precision="mixed") as plan:

@@ -137,6 +137,14 @@ def test_tiles_mixed_match_oracle(n1, n2, nt, T):
     assert relerr_per_channel(V, ref) <= TOL_MIXED
 
 
+def test_tiles_mixed_more_steps_than_stages():
+    """100 samples: seven 16-sample steps, so every shared-memory ring wraps."""
+    n1, n2, nt = 4, 4, 16
+    x = synth.random_complex([n1, n2, nt], 2, 100, seed=93, dtype="ci8", sigma=30.0)
+    V = tile_vis_mixed(synth.Level(n1, n2, (1.0, 0.3, 0.0, 1.0)), offsets(nt, 10), x)
+    assert relerr_per_channel(V, oracle.tile_correlate(n1, n2, nt, x)) <= TOL_MIXED
+
+
 def test_tiles_mixed_full_scale_and_all_ones():
     """+-127 everywhere (the largest spectra FP16 must hold after the 1/16 scale)
     and the layout map of ones, exact after rounding."""
