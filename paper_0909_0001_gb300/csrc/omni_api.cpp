@@ -558,9 +558,14 @@ void choose_chunks(omni_plan* pl) {
     if (sms <= 0) slots = 304;
     // fill one wave of the last pass: as many channels as the slots hold
     pl->Cc = std::min<int64_t>(pl->C, std::max<int64_t>(1, slots / ctas));
-    // one CTA per SM and a long accumulation per CTA: several waves per chunk
-    // keep the tail small (8 channels: 13.5 waves of 152 for 256 CTAs per channel)
-    if (last.kind == KIND_XSPEC5 || last.kind == KIND_COV5) pl->Cc = std::min<int64_t>(pl->C, 8);
+    // one CTA per SM and a long accumulation per CTA, whose epilogue (the fold)
+    // costs about as much as 30 of its 16-sample steps: as many samples per chunk
+    // as the buffer holds for up to 1024 per channel, and several waves per chunk
+    // (6 channels: 10.1 waves of 152 for 256 CTAs per channel)
+    if (last.kind == KIND_XSPEC5 || last.kind == KIND_COV5) {
+        const int64_t per_s = std::max<int64_t>(1, pl->fwd_elems) * (int64_t)sizeof(float2);
+        pl->Cc = std::min<int64_t>(pl->C, std::max<int64_t>(1, std::min<int64_t>(8, (target / per_s) / 1024)));
+    }
     if (pl->knobs.chunk_channels > 0) pl->Cc = std::min<int64_t>(pl->C, pl->knobs.chunk_channels);
     const int64_t per_sample = std::max<int64_t>(1, pl->fwd_elems) * (int64_t)sizeof(float2);
     const int64_t samples = std::max<int64_t>(1, target / per_sample);

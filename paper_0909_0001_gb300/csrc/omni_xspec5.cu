@@ -45,14 +45,16 @@ constexpr int kXT = 64;           // most tiles (2 x 64 = 128 GEMM rows)
 constexpr int kXThreads = 320;    // warps 0-7 convert / epilogue, warp 8 MMA issue, warp 9 TMA
 constexpr int kXProducers = 256;
 constexpr int kXStages = 3;       // shared-memory operand stages
-constexpr int kLBO = 144;         // bytes between K-adjacent core matrices
-constexpr int kSBO = 272;         // bytes between 8-row groups
+constexpr int kLBO = 128;         // bytes between K-adjacent core matrices (dense, 128-byte aligned)
+constexpr int kSBO = 256;         // bytes between 8-row groups
 constexpr int kTileBytes = 16 * kSBO;                 // 128 rows x 16 samples, FP16
 constexpr int kStageBytes = kXF * 2 * kTileBytes;     // per frequency: hi, lo
 // raw spectra brought in by the tensor-memory-access unit, kXRaw steps in
-// flight: one box [sample 16][tile < 64][4 frequencies x (re, im) FP32] per step
+// flight: one box [sample 16][frequency pair 2][tile < 64][2 frequencies x (re, im) FP32]
+// per step (the pair index ahead of the tile index, so that a warp's reads of one
+// pair run over consecutive tiles)
 constexpr int kXRaw = 3;
-constexpr int kRawBytes = 16 * 64 * 32;
+constexpr int kRawBytes = 16 * 2 * 64 * 16;
 // more than half of an SM's shared memory (one CTA per SM, so that two CTAs
 // never ask for 512 tensor-memory columns on the same SM)
 constexpr size_t kXSmem = (size_t)kXStages * kStageBytes + (size_t)kXRaw * kRawBytes + 1024;
@@ -131,11 +133,12 @@ __device__ __forceinline__ void split2(float x0, float x1, uint32_t& hi, uint32_
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(smem_u32(bar)), "r"(bytes));
 }
-// One box of the 3-D tensor map into shared memory, completing on bar.
-__device__ __forceinline__ void tma_load3(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
-    asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
-                 " [%0], [%1, {%2, %3, %4}], [%5];"
-                 :: "r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z),
+// One box of the 4-D tensor map into shared memory, completing on bar.
+__device__ __forceinline__ void tma_load4(void* dst, const CUtensorMap* map, int x, int y, int h, int z,
+                                          uint64_t* bar) {
+    asm volatile("cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+                 " [%0], [%1, {%2, %3, %4, %5}], [%6];"
+                 :: "r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(h), "r"(z),
                     "r"(smem_u32(bar))
                  : "memory");
 }
@@ -197,11 +200,14 @@ __global__ void __launch_bounds__(kXThreads, 1) xspec5(Pass p, PassArgs a, const
     const uint32_t tmem = tmem_slot;
 
     if (warp < 8) {
-        // ---- converters: thread = (tile j, group g of 4 samples of each 16) takes
-        // its 4 x 32 bytes of the step's raw box, splits them into FP16 hi/lo and
-        // writes the operand tiles; samples past the chunk's end (the box runs on
-        // into the next channel) count as zero
-        const int j = tid & 63, g = tid >> 6;
+        // ---- converters: warp w takes tiles 16 (w % 4) .. + 15 and frequency pair
+        // fp = w / 4; lane (tile j, half g of the step's 16 samples) splits its 8
+        // samples x 2 frequencies into FP16 hi/lo and writes, per frequency and
+        // re/im part, one 16-byte core-matrix row (K = 8 samples): a warp's 32 rows
+        // x 16 bytes cover 512 contiguous bytes of a tile, and its raw reads two
+        // 256-byte runs.  Samples past the chunk's end (the box runs on into the
+        // next channel) count as zero.
+        const int j = 16 * (warp & 3) + (tid & 15), g = (tid >> 4) & 1, fp = warp >> 2;
         const bool live = j < NT;
         // spectra from the FP32 tile FFT get the 1/16 here; the tensor-core first
         // pass of a hierarchy already wrote them scaled
@@ -212,41 +218,34 @@ __global__ void __launch_bounds__(kXThreads, 1) xspec5(Pass p, PassArgs a, const
             const int st = n % kXStages, rs = n % kXRaw;
             ok = __all_sync(0xffffffffu, wait_bar(&raw_full[rs], (n / kXRaw) & 1));
             if (!ok) break;
-            float4 cur[4][2];
+            float4 cur[8];  // samples 8 g + q: (re, im) of frequencies 2 fp, 2 fp + 1
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int t = 16 * n + 4 * g + q;
-                if (live && t < tc) {
-                    const float4* r = reinterpret_cast<const float4*>(
-                        raw + (size_t)rs * kRawBytes + ((4 * g + q) * NT + j) * 32);
-                    cur[q][0] = r[0];
-                    cur[q][1] = r[1];
-                } else {
-                    cur[q][0] = cur[q][1] = make_float4(0.f, 0.f, 0.f, 0.f);
-                }
+            for (int q = 0; q < 8; ++q) {
+                const int ts = 8 * g + q, t = 16 * n + ts;
+                cur[q] = (live && t < tc) ? *reinterpret_cast<const float4*>(
+                                                raw + (size_t)rs * kRawBytes + ((ts * 2 + fp) * NT + j) * 16)
+                                          : make_float4(0.f, 0.f, 0.f, 0.f);
             }
             if (n >= kXStages) ok = __all_sync(0xffffffffu, wait_bar(&empty[st], (n / kXStages - 1) & 1));
             if (!ok) break;
             unsigned char* stage = dsm + (size_t)st * kStageBytes;
 #pragma unroll
-            for (int f = 0; f < kXF; ++f) {
-                unsigned char* thi = stage + (2 * f) * kTileBytes;
+            for (int fl = 0; fl < 2; ++fl) {
+                unsigned char* thi = stage + (2 * (2 * fp + fl)) * kTileBytes;
                 unsigned char* tlo = thi + kTileBytes;
 #pragma unroll
                 for (int part = 0; part < 2; ++part) {  // rows j (re) and 64 + j (im)
-                    uint32_t h[2], l[2];
+                    uint32_t h[4], l[4];
 #pragma unroll
-                    for (int q = 0; q < 2; ++q) {
-                        // frequency f of samples 2q, 2q+1: component 2f + part of the 8 floats
-                        const float4 a0 = cur[2 * q][f >> 1], a1 = cur[2 * q + 1][f >> 1];
-                        const int c = 2 * (f & 1) + part;
-                        const float x0 = (c == 0 ? a0.x : c == 1 ? a0.y : c == 2 ? a0.z : a0.w) * in_scale;
-                        const float x1 = (c == 0 ? a1.x : c == 1 ? a1.y : c == 2 ? a1.z : a1.w) * in_scale;
+                    for (int q = 0; q < 4; ++q) {
+                        const float4 a0 = cur[2 * q], a1 = cur[2 * q + 1];
+                        const float x0 = (fl == 0 ? (part == 0 ? a0.x : a0.y) : (part == 0 ? a0.z : a0.w)) * in_scale;
+                        const float x1 = (fl == 0 ? (part == 0 ? a1.x : a1.y) : (part == 0 ? a1.z : a1.w)) * in_scale;
                         split2(x0, x1, h[q], l[q]);
                     }
-                    const int off = tile_off(j + 64 * part, 4 * g);
-                    *reinterpret_cast<uint2*>(thi + off) = make_uint2(h[0], h[1]);
-                    *reinterpret_cast<uint2*>(tlo + off) = make_uint2(l[0], l[1]);
+                    const int off = tile_off(j + 64 * part, 8 * g);
+                    *reinterpret_cast<uint4*>(thi + off) = make_uint4(h[0], h[1], h[2], h[3]);
+                    *reinterpret_cast<uint4*>(tlo + off) = make_uint4(l[0], l[1], l[2], l[3]);
                 }
             }
             // the raw values have been consumed (split and stored) and the operand
@@ -261,7 +260,7 @@ __global__ void __launch_bounds__(kXThreads, 1) xspec5(Pass p, PassArgs a, const
         // ---- warp 9: the tensor-memory-access loads, kXRaw steps ahead; box
         // (x = 8 floats from frequency k0, y = every tile, z = 16 samples)
         bool ok = true;
-        const uint32_t box_bytes = (uint32_t)(16 * NT * 32);
+        const uint32_t box_bytes = (uint32_t)(16 * 2 * NT * 16);
         int issued = 0;
         for (int n = 0; n < steps && ok; ++n) {
             const int rs = n % kXRaw;
@@ -269,7 +268,7 @@ __global__ void __launch_bounds__(kXThreads, 1) xspec5(Pass p, PassArgs a, const
             if (!ok) break;
             if (elect_one()) {
                 mbar_expect_tx(&raw_full[rs], box_bytes);
-                tma_load3(dsm + (size_t)kXStages * kStageBytes + (size_t)rs * kRawBytes, &tmap, (int)(2 * k0), 0,
+                tma_load4(dsm + (size_t)kXStages * kStageBytes + (size_t)rs * kRawBytes, &tmap, (int)(2 * k0), 0, 0,
                           (int)(cc * tc + 16 * n), &raw_full[rs]);
             }
             __syncwarp();
@@ -435,7 +434,9 @@ cudaError_t xspec5_occupancy(int* blocks_per_sm) {
     return e;
 }
 
-// 3-D map of the spectra [samples][tiles][2K floats] for the box of one step.
+// 4-D map of the spectra [samples][tiles][2K floats] viewed as (x: 4 floats of a
+// frequency pair, y: tile, h: which pair of the CTA's four frequencies, z: sample),
+// so that one step's box lands as [z][h][y][x].
 static cudaError_t encode_map(const PassArgs& a, const Pass& p, CUtensorMap* map) {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     static std::once_flag once;
@@ -448,11 +449,11 @@ static cudaError_t encode_map(const PassArgs& a, const Pass& p, CUtensorMap* map
     });
     if (!encode) return cudaErrorNotSupported;
     const cuuint64_t K = (cuuint64_t)p.L, NT = (cuuint64_t)p.outer;
-    const cuuint64_t dims[3] = {2 * K, NT, (cuuint64_t)(a.S * a.tc)};
-    const cuuint64_t strides[2] = {K * 8, NT * K * 8};
-    const cuuint32_t box[3] = {8, (cuuint32_t)NT, 16};
-    const cuuint32_t estr[3] = {1, 1, 1};
-    const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(a.src), dims, strides, box,
+    const cuuint64_t dims[4] = {2 * K, NT, 2, (cuuint64_t)(a.S * a.tc)};
+    const cuuint64_t strides[3] = {K * 8, 16, NT * K * 8};
+    const cuuint32_t box[4] = {4, (cuuint32_t)NT, 2, 16};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void*>(a.src), dims, strides, box,
                               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
