@@ -15,25 +15,27 @@
 // multiplies by 256.
 //
 // CTA = (channel of the chunk, 4 consecutive frequencies); 512 tensor-memory
-// columns hold the 4 accumulators, one CTA per SM.  Warps 0-7 are producers:
-// thread (tile j, group of 4 samples) loads the tile's 4 frequencies for 4
-// samples (32-byte runs, the next step's loads in flight while this step is
-// stored), splits them and writes, per frequency and re/im part, half a
-// 16-byte row of the K-major operand tiles of a shared-memory stage.  Warp 8
-// issues the MMAs (warp-uniform, one elected lane) once a stage is full and
-// releases it through an MMA-completion barrier.  At the end warps 0-7 stage
-// each accumulator in shared memory (lane = row) and add S_ij(k) into the FP64
-// complex accumulator, which for this kernel is laid out [k][i][j] so that a
+// columns hold the 4 accumulators, one CTA per SM.  Warp 9 brings each step's
+// raw spectra (16 samples x every tile x the 4 frequencies, FP32) into a
+// shared-memory ring with one tensor-map box.  Warps 0-7 split them into FP16
+// hi/lo and write the K-major operand tiles of a stage.  Warp 8 issues the MMAs
+// (warp-uniform, one elected lane) once a stage is full and releases it through
+// an MMA-completion barrier.  At the end warps 0-7 combine the four 64 x 64
+// blocks of each G into Re S and Im S in shared memory and fold them into the
+// FP64 accumulator.  EPI_PAIRS adds every S_ij (layout [k][i][j], so that a
 // CTA's update is one contiguous run; launch_xspec5_transpose turns it into
-// the [i][j][k] layout of the inverse passes once per integration.  Every wait
-// is bounded; on expiry the CTA sets the plan's error word, waits (bounded)
-// for its MMAs, frees its tensor memory and returns.
+// the [i][j][k] layout of the inverse passes once per integration).  EPI_LAGS
+// first sums S_ij over the block pairs of each grid offset, one grid axis at a
+// time.  Every wait is bounded; on expiry the CTA sets the plan's error word,
+// waits (bounded) for its MMAs and its copies, frees its tensor memory and
+// returns.
 #include "omni_fft_common.cuh"
 
 #include <cuda.h>            // CUtensorMap; the encoder is fetched from the driver at run time
 #include <cuda_fp16.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 
@@ -50,17 +52,23 @@ constexpr int kSBO = 256;         // bytes between 8-row groups
 constexpr int kTileBytes = 16 * kSBO;                 // 128 rows x 16 samples, FP16
 constexpr int kStageBytes = kXF * 2 * kTileBytes;     // per frequency: hi, lo
 // raw spectra brought in by the tensor-memory-access unit, kXRaw steps in
-// flight: one box [sample 16][frequency pair 2][tile < 64][2 frequencies x (re, im) FP32]
-// per step (the pair index ahead of the tile index, so that a warp's reads of one
-// pair run over consecutive tiles)
+// flight: per step one box of the spectra [sample][tile][K], 16 samples x 64
+// tiles x 4 frequencies x (re, im) FP32 (32-byte rows), landing as
+// [sample][tile][4 frequencies]
 constexpr int kXRaw = 3;
 constexpr int kRawBytes = 16 * 2 * 64 * 16;
+// epilogue staging in the (then idle) stage and raw buffers: per frequency the
+// real and imaginary 64 x 64 cross-spectrum matrices, and the partial lag sums
+constexpr int kEp = 68;                               // floats per row (conflict-free 16-byte rows)
+constexpr int kEpMat = 64 * kEp;                      // floats per matrix
+constexpr int kMaxU = 960;                            // partial sums per frequency (8 x 8 grid: 8 x 8 x 15)
+static_assert(kXF * 2 * kEpMat * 4 + kXF * kMaxU * 8 <= kXStages * kStageBytes + kXRaw * kRawBytes,
+              "epilogue staging fits the pipeline buffers");
 // more than half of an SM's shared memory (one CTA per SM, so that two CTAs
 // never ask for 512 tensor-memory columns on the same SM)
 constexpr size_t kXSmem = (size_t)kXStages * kStageBytes + (size_t)kXRaw * kRawBytes + 1024;
 static_assert(kXSmem > 114 * 1024 && kXSmem <= 227 * 1024, "one CTA per SM");
 constexpr uint32_t kTmemCols = 512;
-constexpr int kGsPitch = 132;     // floats per row of the epilogue's staging of G (conflict-free)
 constexpr float kXScale = 1.0f / 16.0f;
 constexpr double kXFold = 256.0;
 // kind::f16, FP32 accumulate, FP16 A and B, K-major, M = 128, N = 128
@@ -133,12 +141,11 @@ __device__ __forceinline__ void split2(float x0, float x1, uint32_t& hi, uint32_
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(smem_u32(bar)), "r"(bytes));
 }
-// One box of the 4-D tensor map into shared memory, completing on bar.
-__device__ __forceinline__ void tma_load4(void* dst, const CUtensorMap* map, int x, int y, int h, int z,
-                                          uint64_t* bar) {
-    asm volatile("cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
-                 " [%0], [%1, {%2, %3, %4, %5}], [%6];"
-                 :: "r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(h), "r"(z),
+// One box of the 3-D tensor map into shared memory, completing on bar.
+__device__ __forceinline__ void tma_load3(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
+    asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+                 " [%0], [%1, {%2, %3, %4}], [%5];"
+                 :: "r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z),
                     "r"(smem_u32(bar))
                  : "memory");
 }
@@ -200,14 +207,14 @@ __global__ void __launch_bounds__(kXThreads, 1) xspec5(Pass p, PassArgs a, const
     const uint32_t tmem = tmem_slot;
 
     if (warp < 8) {
-        // ---- converters: warp w takes tiles 16 (w % 4) .. + 15 and frequency pair
-        // fp = w / 4; lane (tile j, half g of the step's 16 samples) splits its 8
-        // samples x 2 frequencies into FP16 hi/lo and writes, per frequency and
-        // re/im part, one 16-byte core-matrix row (K = 8 samples): a warp's 32 rows
-        // x 16 bytes cover 512 contiguous bytes of a tile, and its raw reads two
-        // 256-byte runs.  Samples past the chunk's end (the box runs on into the
-        // next channel) count as zero.
-        const int j = 16 * (warp & 3) + (tid & 15), g = (tid >> 4) & 1, fp = warp >> 2;
+        // ---- converters: warp w takes tiles 16 (w % 4) .. + 15 and half g = w / 4
+        // of the step's 16 samples; lane (tile j, frequency pair fp = lane / 16)
+        // splits its 8 samples x 2 frequencies into FP16 hi/lo and writes, per
+        // frequency and re/im part, one 16-byte core-matrix row (K = 8 samples).  A
+        // warp's raw reads are 512 contiguous bytes and its operand writes 4 whole
+        // 128-byte runs (no bank conflicts).  Samples past the chunk's end (the box
+        // runs on into the next channel) count as zero.
+        const int j = 16 * (warp & 3) + (tid & 15), g = warp >> 2, fp = (tid >> 4) & 1;
         const bool live = j < NT;
         // spectra from the FP32 tile FFT get the 1/16 here; the tensor-core first
         // pass of a hierarchy already wrote them scaled
@@ -223,7 +230,7 @@ __global__ void __launch_bounds__(kXThreads, 1) xspec5(Pass p, PassArgs a, const
             for (int q = 0; q < 8; ++q) {
                 const int ts = 8 * g + q, t = 16 * n + ts;
                 cur[q] = (live && t < tc) ? *reinterpret_cast<const float4*>(
-                                                raw + (size_t)rs * kRawBytes + ((ts * 2 + fp) * NT + j) * 16)
+                                                raw + (size_t)rs * kRawBytes + ((ts * NT + j) * 2 + fp) * 16)
                                           : make_float4(0.f, 0.f, 0.f, 0.f);
             }
             if (n >= kXStages) ok = __all_sync(0xffffffffu, wait_bar(&empty[st], (n / kXStages - 1) & 1));
@@ -257,19 +264,19 @@ __global__ void __launch_bounds__(kXThreads, 1) xspec5(Pass p, PassArgs a, const
         }
         if (!ok) atomicExch(&abort_flag, 1);
     } else if (warp == 9) {
-        // ---- warp 9: the tensor-memory-access loads, kXRaw steps ahead; box
-        // (x = 8 floats from frequency k0, y = every tile, z = 16 samples)
+        // ---- warp 9: the raw loads, kXRaw steps ahead: one tensor-map box (x = 8
+        // floats from frequency k0, y = every tile, z = 16 samples) per step
         bool ok = true;
-        const uint32_t box_bytes = (uint32_t)(16 * 2 * NT * 16);
+        const uint32_t box_bytes = (uint32_t)(16 * NT * 32);
         int issued = 0;
         for (int n = 0; n < steps && ok; ++n) {
             const int rs = n % kXRaw;
             if (n >= kXRaw) ok = __all_sync(0xffffffffu, wait_bar(&raw_empty[rs], (n / kXRaw - 1) & 1));
             if (!ok) break;
+            unsigned char* slot = dsm + (size_t)kXStages * kStageBytes + (size_t)rs * kRawBytes;
             if (elect_one()) {
                 mbar_expect_tx(&raw_full[rs], box_bytes);
-                tma_load4(dsm + (size_t)kXStages * kStageBytes + (size_t)rs * kRawBytes, &tmap, (int)(2 * k0), 0, 0,
-                          (int)(cc * tc + 16 * n), &raw_full[rs]);
+                tma_load3(slot, &tmap, (int)(2 * k0), 0, (int)(cc * tc + 16 * n), &raw_full[rs]);
             }
             __syncwarp();
             issued = n + 1;
@@ -304,6 +311,18 @@ __global__ void __launch_bounds__(kXThreads, 1) xspec5(Pass p, PassArgs a, const
     }
     __syncthreads();
     bool fine = abort_flag == 0;
+    // lag sums: this CTA's 4 Q2 accumulator values (contiguous, k-major), loaded
+    // while the last MMAs run
+    const int n3 = p.L1, n4 = p.L2, w3 = 2 * n3 - 1, Q2 = w3 * (2 * n4 - 1);
+    double2* S = reinterpret_cast<double2*>(a.P + (a.c0 + cc) * a.P_stride);
+    double2 pre[4];
+    if (EPI == EPI_LAGS && warp < 8 && fine && steps > 0) {
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int e = tid + kXProducers * m;
+            if (e < kXF * Q2) pre[m] = S[k0 * Q2 + e];
+        }
+    }
     if (warp < 8 && fine && steps > 0) {
         // accumulators complete
         fine = __all_sync(0xffffffffu, wait_bar(&done, 0));
@@ -313,74 +332,116 @@ __global__ void __launch_bounds__(kXThreads, 1) xspec5(Pass p, PassArgs a, const
         if (warp == 8) wait_bar(&done, 0);  // its MMAs finish before the memory is freed
     } else if (steps > 0) {
         tc_after_sync();
-        // epilogue, per frequency: every row of G_f to shared memory (warps w and
-        // w + 4 read the two column halves of lanes 32 (w % 4) ..), then thread
-        // (i parity, j) adds S_ij(k) = (G[i][j] + G[64+i][64+j]) + i (G[64+i][j] -
-        // G[i][64+j]) to the accumulator [k][i][j]: consecutive threads,
-        // consecutive j, so a warp's accesses are 512 contiguous bytes
-        float* gs = reinterpret_cast<float*>(dsm);  // [128][kGsPitch], the stages are free now
-        double2* S = reinterpret_cast<double2*>(a.P + (a.c0 + cc) * a.P_stride);
-        const uint32_t lane_addr = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
-        const int r = 32 * (warp & 3) + (tid & 31), half = (warp >> 2) & 1;
-        for (int f = 0; f < kXF; ++f) {
-            if (warp < 8) {
+        // epilogue: S_ij(k) = (G[i][j] + G[64+i][64+j]) + i (G[64+i][j] - G[i][64+j])
+        // for the 4 frequencies into shared memory as Re[f][i][j], Im[f][i][j].  Warp
+        // (lane quarter q = w % 4, column half h = w / 4) reads rows 32 q + lane of
+        // tensor memory; the rows i < 64 store their parts, then the rows 64 + i add
+        // theirs (each thread its own row of the two matrices, no races).
+        float* mats = reinterpret_cast<float*>(dsm);  // the stage and raw buffers are free now
+        const int q = warp & 3, h = (warp >> 2) & 1;
+        const uint32_t lane_addr = tmem + ((uint32_t)(32 * q) << 16);
+        const int i = 32 * (q & 1) + (tid & 31);
+        for (int phase = 0; phase < 2; ++phase) {
+            if (warp < 8 && (q >> 1) == phase) {
+                for (int f = 0; f < kXF; ++f) {
+                    // phase 0: h = 0 -> Re (G[i][c]), h = 1 -> Im (-G[i][64 + c]);
+                    // phase 1: h = 0 -> Im (+G[64 + i][c]), h = 1 -> Re (+G[64 + i][64 + c])
+                    float* row = mats + (2 * f + (h ^ phase)) * kEpMat + i * kEp;
+                    const float sign = (phase == 0 && h == 1) ? -1.f : 1.f;
 #pragma unroll
-                for (int c0 = 0; c0 < 64; c0 += 32) {
-                    float v[32];
-                    ld32(lane_addr + 128 * f + 64 * half + c0, v);
+                    for (int c0 = 0; c0 < 64; c0 += 32) {
+                        float v[32];
+                        ld32(lane_addr + 128 * f + 64 * h + c0, v);
 #pragma unroll
-                    for (int q = 0; q < 32; q += 4)
-                        *reinterpret_cast<float4*>(gs + r * kGsPitch + 64 * half + c0 + q) =
-                            make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+                        for (int c = 0; c < 32; c += 4) {
+                            float4* d = reinterpret_cast<float4*>(row + c0 + c);
+                            float4 o = phase ? *d : make_float4(0.f, 0.f, 0.f, 0.f);
+                            o.x += sign * v[c];
+                            o.y += sign * v[c + 1];
+                            o.z += sign * v[c + 2];
+                            o.w += sign * v[c + 3];
+                            *d = o;
+                        }
+                    }
                 }
             }
             __syncthreads();
-            if (EPI == EPI_PAIRS && warp < 8) {
-                const int jj = tid & 63, ih = tid >> 6;  // i = ih, ih + 4, ...
-                if (jj < NT) {
+        }
+        if (EPI == EPI_PAIRS && warp < 8) {
+            // thread (i parity, j) adds S_ij(k) to the accumulator [k][i][j]: consecutive
+            // threads, consecutive j, so a warp's accesses are 512 contiguous bytes
+            const int jj = tid & 63, ih = tid >> 6;  // i = ih, ih + 4, ...
+            if (jj < NT) {
+                for (int f = 0; f < kXF; ++f) {
+                    const float* re = mats + (2 * f) * kEpMat;
+                    const float* im = re + kEpMat;
                     double2* col = S + ((k0 + f) * (int64_t)NT) * NT + jj;
                     constexpr int kIB = 16;  // accumulator loads in flight per thread
                     for (int i0 = ih; i0 < NT; i0 += 4 * kIB) {
                         double2 cur[kIB];
 #pragma unroll
                         for (int u = 0; u < kIB; ++u) {
-                            const int i = i0 + 4 * u;
-                            if (i < NT) cur[u] = col[(int64_t)i * NT];
+                            const int ii = i0 + 4 * u;
+                            if (ii < NT) cur[u] = col[(int64_t)ii * NT];
                         }
 #pragma unroll
                         for (int u = 0; u < kIB; ++u) {
-                            const int i = i0 + 4 * u;
-                            if (i < NT) {
-                                const float* gi = gs + i * kGsPitch;
-                                const float* gb = gs + (64 + i) * kGsPitch;
-                                cur[u].x += kXFold * ((double)gi[jj] + (double)gb[64 + jj]);
-                                cur[u].y += kXFold * ((double)gb[jj] - (double)gi[64 + jj]);
-                                col[(int64_t)i * NT] = cur[u];
+                            const int ii = i0 + 4 * u;
+                            if (ii < NT) {
+                                cur[u].x += kXFold * (double)re[ii * kEp + jj];
+                                cur[u].y += kXFold * (double)im[ii * kEp + jj];
+                                col[(int64_t)ii * NT] = cur[u];
                             }
                         }
                     }
                 }
             }
-            if (EPI == EPI_LAGS && warp < 8) {
-                // q2 per thread: the sum of S_ij over the block pairs of one grid offset
-                const int n3 = p.L1, n4 = p.L2, w3 = 2 * n3 - 1, Q2 = w3 * (2 * n4 - 1);
-                for (int q2 = tid; q2 < Q2; q2 += kXProducers) {
-                    const int d3 = q2 % w3 - (n3 - 1), d4 = q2 / w3 - (n4 - 1);
-                    float re = 0.f, im = 0.f;
-                    for (int m4 = max(0, -d4); m4 < min(n4, n4 - d4); ++m4)
-                        for (int m3 = max(0, -d3); m3 < min(n3, n3 - d3); ++m3) {
-                            const int jb = m3 + n3 * m4, ib = jb + d3 + n3 * d4;
-                            const float* gi = gs + ib * kGsPitch;
-                            const float* gb = gs + (64 + ib) * kGsPitch;
-                            re += gi[jb] + gb[64 + jb];
-                            im += gb[jb] - gi[64 + jb];
-                        }
-                    double2& r = S[(k0 + f) * (int64_t)Q2 + q2];
-                    r.x += kXFold * (double)re;
-                    r.y += kXFold * (double)im;
+        }
+        if (EPI == EPI_LAGS && warp < 8) {
+            // the sum over block pairs of equal grid offset, one axis at a time: with
+            // block i = a_A s_A + a_B s_B (A the longer grid axis),
+            //   U[f][a_B][b_B][d_A] = sum_{a_A} S_{(a_A, a_B), (a_A - d_A, b_B)}
+            //   R[f][d_A][d_B]      = sum_{a_B} U[f][a_B][a_B - d_B][d_A]
+            // (at most max(n3, n4) terms per output instead of n3 n4)
+            const bool a3 = n3 >= n4;
+            const int na = a3 ? n3 : n4, nb = a3 ? n4 : n3, sA = a3 ? 1 : n3, sB = a3 ? n3 : 1;
+            const int wA = 2 * na - 1, nU = nb * nb * wA;
+            float2* U = reinterpret_cast<float2*>(mats + kXF * 2 * kEpMat);
+            for (int o = tid; o < kXF * nU; o += kXProducers) {
+                const int dAi = o % wA, r0 = o / wA, bB = r0 % nb, r1 = r0 / nb, aB = r1 % nb, f = r1 / nb;
+                const int dA = dAi - (na - 1);
+                const float* re = mats + (2 * f) * kEpMat;
+                const float* im = re + kEpMat;
+                const int rowb = aB * sB, colb = bB * sB - dA * sA;
+                float sr = 0.f, si = 0.f;
+                for (int aA = max(0, dA); aA < min(na, na + dA); ++aA) {
+                    const int at = (rowb + aA * sA) * kEp + colb + aA * sA;
+                    sr += re[at];
+                    si += im[at];
                 }
+                U[o] = make_float2(sr, si);
             }
             __syncthreads();
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                const int e = tid + kXProducers * m;
+                if (e < kXF * Q2) {
+                    const int f = e / Q2, q2 = e - f * Q2;
+                    const int d3 = q2 % w3 - (n3 - 1), d4 = q2 / w3 - (n4 - 1);
+                    const int dA = a3 ? d3 : d4, dB = a3 ? d4 : d3;
+                    const float2* Uf = U + f * nU + dA + na - 1;
+                    float sr = 0.f, si = 0.f;
+                    for (int aB = max(0, dB); aB < min(nb, nb + dB); ++aB) {
+                        const float2 u = Uf[(aB * nb + aB - dB) * wA];
+                        sr += u.x;
+                        si += u.y;
+                    }
+                    double2 r = pre[m];
+                    r.x += kXFold * (double)sr;
+                    r.y += kXFold * (double)si;
+                    S[k0 * Q2 + e] = r;
+                }
+            }
         }
     }
     tc_before_sync();
@@ -434,9 +495,8 @@ cudaError_t xspec5_occupancy(int* blocks_per_sm) {
     return e;
 }
 
-// 4-D map of the spectra [samples][tiles][2K floats] viewed as (x: 4 floats of a
-// frequency pair, y: tile, h: which pair of the CTA's four frequencies, z: sample),
-// so that one step's box lands as [z][h][y][x].
+// 3-D map of the spectra [samples][tiles][2K floats]; a box (x: the 8 floats of
+// the CTA's 4 frequencies, y: every tile, z: 16 samples) lands as [z][y][x].
 static cudaError_t encode_map(const PassArgs& a, const Pass& p, CUtensorMap* map) {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     static std::once_flag once;
@@ -449,11 +509,11 @@ static cudaError_t encode_map(const PassArgs& a, const Pass& p, CUtensorMap* map
     });
     if (!encode) return cudaErrorNotSupported;
     const cuuint64_t K = (cuuint64_t)p.L, NT = (cuuint64_t)p.outer;
-    const cuuint64_t dims[4] = {2 * K, NT, 2, (cuuint64_t)(a.S * a.tc)};
-    const cuuint64_t strides[3] = {K * 8, 16, NT * K * 8};
-    const cuuint32_t box[4] = {4, (cuuint32_t)NT, 2, 16};
-    const cuuint32_t estr[4] = {1, 1, 1, 1};
-    const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void*>(a.src), dims, strides, box,
+    const cuuint64_t dims[3] = {2 * K, NT, (cuuint64_t)(a.S * a.tc)};
+    const cuuint64_t strides[2] = {K * 8, NT * K * 8};
+    const cuuint32_t box[3] = {8, (cuuint32_t)NT, 16};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(a.src), dims, strides, box,
                               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
@@ -466,10 +526,12 @@ cudaError_t launch_xspec5(const Pass& p, const PassArgs& a, cudaStream_t st) {
     // the TMA unit wants a 16-byte aligned base and row pitches
     if (reinterpret_cast<uintptr_t>(a.src) % 16 || (p.L * 8) % 16) return cudaErrorInvalidValue;
     CUtensorMap map;
-    cudaError_t me = encode_map(a, p, &map);
+    const cudaError_t me = encode_map(a, p, &map);
     if (me != cudaSuccess) return me;
     if (p.kind == KIND_COV5) {
         if (p.L1 < 1 || p.L2 < 1 || p.L1 * p.L2 != p.outer) return cudaErrorInvalidValue;
+        const int na = std::max(p.L1, p.L2), nb = std::min(p.L1, p.L2);
+        if (nb * nb * (2 * na - 1) > kMaxU) return cudaErrorInvalidValue;
         cudaError_t e = smem_limit_once((const void*)xspec5<EPI_LAGS>, kXSmem);
         if (e != cudaSuccess) return e;
         xspec5<EPI_LAGS><<<(unsigned)blocks, kXThreads, kXSmem, st>>>(p, a, map);
