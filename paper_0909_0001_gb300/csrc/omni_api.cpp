@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
+#include <cstdint>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -558,18 +559,29 @@ void choose_chunks(omni_plan* pl) {
     if (sms <= 0) slots = 304;
     // fill one wave of the last pass: as many channels as the slots hold
     pl->Cc = std::min<int64_t>(pl->C, std::max<int64_t>(1, slots / ctas));
-    // one CTA per SM and a long accumulation per CTA, whose epilogue (the fold)
-    // costs about as much as 30 of its 16-sample steps: as many samples per chunk
-    // as the buffer holds for up to 1024 per channel, and several waves per chunk
-    // (6 channels: 10.1 waves of 152 for 256 CTAs per channel)
-    if (last.kind == KIND_XSPEC5 || last.kind == KIND_COV5) {
-        const int64_t per_s = std::max<int64_t>(1, pl->fwd_elems) * (int64_t)sizeof(float2);
-        pl->Cc = std::min<int64_t>(pl->C, std::max<int64_t>(1, std::min<int64_t>(8, (target / per_s) / 1024)));
+    const int64_t per_sample = std::max<int64_t>(1, pl->fwd_elems) * (int64_t)sizeof(float2);
+    const bool gemm_last = last.kind == KIND_XSPEC5 || last.kind == KIND_COV5;
+    if (gemm_last) {
+        // one CTA per SM and a long accumulation per CTA (its epilogue costs several
+        // of its 16-sample steps): 1024 samples per chunk, and channels per chunk
+        // chosen so that the chunks' CTAs fill whole waves (256 CTAs per channel on
+        // 152 SMs: 6-channel chunks run 10.1 waves in 11, 16-channel chunks 26.9 in
+        // 27), within four times the chunk-buffer target (equal ties: fewer channels)
+        const int64_t cap = 4 * target;
+        pl->Tc = std::max<int64_t>(1, std::min<int64_t>(1024, cap / per_sample));
+        const int64_t cmax = std::min<int64_t>(pl->C, std::max<int64_t>(1, cap / (per_sample * pl->Tc)));
+        const int64_t sl = sms > 0 ? (int64_t)sms * std::max(per_sm, 1) : 152;  // one CTA per SM
+        int64_t best = 1, best_waves = INT64_MAX;
+        for (int64_t cc = 1; cc <= cmax; ++cc) {
+            const int64_t n = (pl->C + cc - 1) / cc, cb = (pl->C + n - 1) / n, tail = pl->C - (n - 1) * cb;
+            const int64_t waves = (n - 1) * ((cb * ctas + sl - 1) / sl) + (tail * ctas + sl - 1) / sl;
+            if (waves < best_waves) best = cc, best_waves = waves;
+        }
+        pl->Cc = best;
     }
     if (pl->knobs.chunk_channels > 0) pl->Cc = std::min<int64_t>(pl->C, pl->knobs.chunk_channels);
-    const int64_t per_sample = std::max<int64_t>(1, pl->fwd_elems) * (int64_t)sizeof(float2);
     const int64_t samples = std::max<int64_t>(1, target / per_sample);
-    pl->Tc = std::max<int64_t>(1, std::min<int64_t>(1024, samples / pl->Cc));
+    if (!gemm_last) pl->Tc = std::max<int64_t>(1, std::min<int64_t>(1024, samples / pl->Cc));
     const int64_t per_chan = std::max<int64_t>(1, pl->inv_elems) * (int64_t)sizeof(float2);
     pl->Cv = std::min<int64_t>(pl->C, std::max<int64_t>(1, target / per_chan));
     pl->buf_elems = std::max(pl->Cc * pl->Tc * pl->fwd_elems, pl->Cv * pl->inv_elems);

@@ -62,7 +62,8 @@ constexpr int kRawBytes = 16 * 2 * 64 * 16;
 constexpr int kEp = 68;                               // floats per row (conflict-free 16-byte rows)
 constexpr int kEpMat = 64 * kEp;                      // floats per matrix
 constexpr int kMaxU = 960;                            // partial sums per frequency (8 x 8 grid: 8 x 8 x 15)
-static_assert(kXF * 2 * kEpMat * 4 + kXF * kMaxU * 8 <= kXStages * kStageBytes + kXRaw * kRawBytes,
+constexpr int kMaxQ2 = 225;                           // coarse lags of at most 64 blocks (8 x 8: 15 x 15)
+static_assert(kXF * 2 * kEpMat * 4 + kXF * (kMaxU + kMaxQ2) * 8 <= kXStages * kStageBytes + kXRaw * kRawBytes,
               "epilogue staging fits the pipeline buffers");
 // more than half of an SM's shared memory (one CTA per SM, so that two CTAs
 // never ask for 512 tensor-memory columns on the same SM)
@@ -110,21 +111,29 @@ __device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, long lo
         if (clock64() - t0 > budget) return false;
     }
 }
-__device__ __forceinline__ void ld32(uint32_t taddr, float (&v)[32]) {
-    uint32_t r[32];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
-                   "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
-                   "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]),
-                   "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-                   "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
-                   "=r"(r[30]), "=r"(r[31])
-                 : "r"(taddr));
+// 64 consecutive columns of the warp's 32 lanes: two loads, one wait
+__device__ __forceinline__ void ld64(uint32_t taddr, float (&v)[64]) {
+    uint32_t r[64];
+#pragma unroll
+    for (int half = 0; half < 2; ++half)
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                     "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                     "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                     : "=r"(r[32 * half + 0]), "=r"(r[32 * half + 1]), "=r"(r[32 * half + 2]),
+                       "=r"(r[32 * half + 3]), "=r"(r[32 * half + 4]), "=r"(r[32 * half + 5]),
+                       "=r"(r[32 * half + 6]), "=r"(r[32 * half + 7]), "=r"(r[32 * half + 8]),
+                       "=r"(r[32 * half + 9]), "=r"(r[32 * half + 10]), "=r"(r[32 * half + 11]),
+                       "=r"(r[32 * half + 12]), "=r"(r[32 * half + 13]), "=r"(r[32 * half + 14]),
+                       "=r"(r[32 * half + 15]), "=r"(r[32 * half + 16]), "=r"(r[32 * half + 17]),
+                       "=r"(r[32 * half + 18]), "=r"(r[32 * half + 19]), "=r"(r[32 * half + 20]),
+                       "=r"(r[32 * half + 21]), "=r"(r[32 * half + 22]), "=r"(r[32 * half + 23]),
+                       "=r"(r[32 * half + 24]), "=r"(r[32 * half + 25]), "=r"(r[32 * half + 26]),
+                       "=r"(r[32 * half + 27]), "=r"(r[32 * half + 28]), "=r"(r[32 * half + 29]),
+                       "=r"(r[32 * half + 30]), "=r"(r[32 * half + 31])
+                     : "r"(taddr + 32 * half));
     asm volatile("tcgen05.wait::ld.sync.aligned;");
 #pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+    for (int i = 0; i < 64; ++i) v[i] = __uint_as_float(r[i]);
 }
 __device__ __forceinline__ uint32_t h2u(__half2 h) {
     uint32_t u;
@@ -341,32 +350,32 @@ __global__ void __launch_bounds__(kXThreads, 1) xspec5(Pass p, PassArgs a, const
         const int q = warp & 3, h = (warp >> 2) & 1;
         const uint32_t lane_addr = tmem + ((uint32_t)(32 * q) << 16);
         const int i = 32 * (q & 1) + (tid & 31);
-        for (int phase = 0; phase < 2; ++phase) {
-            if (warp < 8 && (q >> 1) == phase) {
-                for (int f = 0; f < kXF; ++f) {
-                    // phase 0: h = 0 -> Re (G[i][c]), h = 1 -> Im (-G[i][64 + c]);
-                    // phase 1: h = 0 -> Im (+G[64 + i][c]), h = 1 -> Re (+G[64 + i][64 + c])
-                    float* row = mats + (2 * f + (h ^ phase)) * kEpMat + i * kEp;
-                    const float sign = (phase == 0 && h == 1) ? -1.f : 1.f;
+        if (warp < 8) {
+            // the upper-row warps store frequency f while the lower-row warps add
+            // frequency f - 1 (named barrier 1 + f between them)
+            const int phase = q >> 1;
+            for (int f = 0; f < kXF; ++f) {
+                if (phase) asm volatile("bar.sync %0, %1;" :: "r"(1 + f), "r"(kXProducers) : "memory");
+                // phase 0: h = 0 -> Re (G[i][c]), h = 1 -> Im (-G[i][64 + c]);
+                // phase 1: h = 0 -> Im (+G[64 + i][c]), h = 1 -> Re (+G[64 + i][64 + c])
+                float* row = mats + (2 * f + (h ^ phase)) * kEpMat + i * kEp;
+                const float sign = (phase == 0 && h == 1) ? -1.f : 1.f;
+                float v[64];
+                ld64(lane_addr + 128 * f + 64 * h, v);
 #pragma unroll
-                    for (int c0 = 0; c0 < 64; c0 += 32) {
-                        float v[32];
-                        ld32(lane_addr + 128 * f + 64 * h + c0, v);
-#pragma unroll
-                        for (int c = 0; c < 32; c += 4) {
-                            float4* d = reinterpret_cast<float4*>(row + c0 + c);
-                            float4 o = phase ? *d : make_float4(0.f, 0.f, 0.f, 0.f);
-                            o.x += sign * v[c];
-                            o.y += sign * v[c + 1];
-                            o.z += sign * v[c + 2];
-                            o.w += sign * v[c + 3];
-                            *d = o;
-                        }
-                    }
+                for (int c = 0; c < 64; c += 4) {
+                    float4* d = reinterpret_cast<float4*>(row + c);
+                    float4 o = phase ? *d : make_float4(0.f, 0.f, 0.f, 0.f);
+                    o.x += sign * v[c];
+                    o.y += sign * v[c + 1];
+                    o.z += sign * v[c + 2];
+                    o.w += sign * v[c + 3];
+                    *d = o;
                 }
+                if (!phase) asm volatile("bar.arrive %0, %1;" :: "r"(1 + f), "r"(kXProducers) : "memory");
             }
-            __syncthreads();
         }
+        __syncthreads();
         if (EPI == EPI_PAIRS && warp < 8) {
             // thread (i parity, j) adds S_ij(k) to the accumulator [k][i][j]: consecutive
             // threads, consecutive j, so a warp's accesses are 512 contiguous bytes
@@ -397,7 +406,7 @@ __global__ void __launch_bounds__(kXThreads, 1) xspec5(Pass p, PassArgs a, const
                 }
             }
         }
-        if (EPI == EPI_LAGS && warp < 8) {
+        if (EPI == EPI_LAGS) {
             // the sum over block pairs of equal grid offset, one axis at a time: with
             // block i = a_A s_A + a_B s_B (A the longer grid axis),
             //   U[f][a_B][b_B][d_A] = sum_{a_A} S_{(a_A, a_B), (a_A - d_A, b_B)}
@@ -405,40 +414,90 @@ __global__ void __launch_bounds__(kXThreads, 1) xspec5(Pass p, PassArgs a, const
             // (at most max(n3, n4) terms per output instead of n3 n4)
             const bool a3 = n3 >= n4;
             const int na = a3 ? n3 : n4, nb = a3 ? n4 : n3, sA = a3 ? 1 : n3, sB = a3 ? n3 : 1;
-            const int wA = 2 * na - 1, nU = nb * nb * wA;
+            const int wA = 2 * na - 1, wB = 2 * nb - 1, nU = nb * nb * wA;
             float2* U = reinterpret_cast<float2*>(mats + kXF * 2 * kEpMat);
-            for (int o = tid; o < kXF * nU; o += kXProducers) {
-                const int dAi = o % wA, r0 = o / wA, bB = r0 % nb, r1 = r0 / nb, aB = r1 % nb, f = r1 / nb;
-                const int dA = dAi - (na - 1);
-                const float* re = mats + (2 * f) * kEpMat;
-                const float* im = re + kEpMat;
-                const int rowb = aB * sB, colb = bB * sB - dA * sA;
-                float sr = 0.f, si = 0.f;
-                for (int aA = max(0, dA); aA < min(na, na + dA); ++aA) {
-                    const int at = (rowb + aA * sA) * kEp + colb + aA * sA;
-                    sr += re[at];
-                    si += im[at];
+            float2* R = U + kXF * nU;
+            const int lane = tid & 31;
+            // stage 1, warp task (f, a_B, 8 offsets d_A, 4 blocks b_B): every lane of
+            // the warp at the same a_A, so its reads are 32 distinct words of one row;
+            // the 10 warps take consecutive runs of tasks, 8 a_A per batch of loads
+            {
+                const int ndg = (wA + 7) / 8, nbg = (nb + 3) / 4, ntask = kXF * nb * nbg * ndg;
+                const int ld = lane & 7, lb = lane >> 3;
+                const int t0 = warp * ntask / 10, t1 = (warp + 1) * ntask / 10;
+                int dg = t0 % ndg, bg = (t0 / ndg) % nbg, aB = (t0 / (ndg * nbg)) % nb, f = t0 / (ndg * nbg * nb);
+                for (int task = t0; task < t1; ++task) {
+                    const int dAi = 8 * dg + ld, bB = 4 * bg + lb, dA = dAi - (na - 1);
+                    const bool live = dAi < wA && bB < nb;
+                    const float* re = mats + (2 * f) * kEpMat + (aB * sB) * kEp + bB * sB - dA * sA;
+                    const float* im = re + kEpMat;
+                    float sr = 0.f, si = 0.f;
+                    for (int a0 = 0; a0 < na; a0 += 8) {
+                        float vr[8], vi[8];
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            const int aA = a0 + u;
+                            const bool ok = live && aA < na && aA - dA >= 0 && aA - dA < na;
+                            vr[u] = ok ? re[aA * sA * (kEp + 1)] : 0.f;
+                            vi[u] = ok ? im[aA * sA * (kEp + 1)] : 0.f;
+                        }
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            sr += vr[u];
+                            si += vi[u];
+                        }
+                    }
+                    if (live) U[((f * nb + aB) * nb + bB) * wA + dAi] = make_float2(sr, si);
+                    if (++dg == ndg) {
+                        dg = 0;
+                        if (++bg == nbg) {
+                            bg = 0;
+                            if (++aB == nb) aB = 0, ++f;
+                        }
+                    }
                 }
-                U[o] = make_float2(sr, si);
+            }
+            __syncthreads();
+            // stage 2, warp task (f, d_B, 32 offsets d_A)
+            {
+                const int ndg = (wA + 31) / 32, ntask = kXF * wB * ndg;
+                const int t0 = warp * ntask / 10, t1 = (warp + 1) * ntask / 10;
+                int dg = t0 % ndg, dBi = (t0 / ndg) % wB, f = t0 / (ndg * wB);
+                for (int task = t0; task < t1; ++task) {
+                    const int dAi = 32 * dg + lane, dB = dBi - (nb - 1);
+                    if (dAi < wA) {
+                        const float2* Uf = U + f * nU + dAi;
+                        float sr = 0.f, si = 0.f;
+                        for (int a0 = 0; a0 < nb; a0 += 8) {
+                            float2 v[8];
+#pragma unroll
+                            for (int u = 0; u < 8; ++u) {
+                                const int aB = a0 + u;
+                                const bool ok = aB < nb && aB - dB >= 0 && aB - dB < nb;
+                                v[u] = ok ? Uf[(aB * nb + aB - dB) * wA] : make_float2(0.f, 0.f);
+                            }
+#pragma unroll
+                            for (int u = 0; u < 8; ++u) {
+                                sr += v[u].x;
+                                si += v[u].y;
+                            }
+                        }
+                        R[f * Q2 + (a3 ? dAi + w3 * dBi : dBi + w3 * dAi)] = make_float2(sr, si);
+                    }
+                    if (++dg == ndg) {
+                        dg = 0;
+                        if (++dBi == wB) dBi = 0, ++f;
+                    }
+                }
             }
             __syncthreads();
 #pragma unroll
             for (int m = 0; m < 4; ++m) {
                 const int e = tid + kXProducers * m;
-                if (e < kXF * Q2) {
-                    const int f = e / Q2, q2 = e - f * Q2;
-                    const int d3 = q2 % w3 - (n3 - 1), d4 = q2 / w3 - (n4 - 1);
-                    const int dA = a3 ? d3 : d4, dB = a3 ? d4 : d3;
-                    const float2* Uf = U + f * nU + dA + na - 1;
-                    float sr = 0.f, si = 0.f;
-                    for (int aB = max(0, dB); aB < min(nb, nb + dB); ++aB) {
-                        const float2 u = Uf[(aB * nb + aB - dB) * wA];
-                        sr += u.x;
-                        si += u.y;
-                    }
+                if (warp < 8 && e < kXF * Q2) {
                     double2 r = pre[m];
-                    r.x += kXFold * (double)sr;
-                    r.y += kXFold * (double)si;
+                    r.x += kXFold * (double)R[e].x;
+                    r.y += kXFold * (double)R[e].y;
                     S[k0 * Q2 + e] = r;
                 }
             }
