@@ -150,7 +150,8 @@ class ClockSampler:
 # ------------------------------------------------------------------ roofline
 
 # kernel sources behind each pass kind (plus the shared headers)
-_PASS_SOURCES = [("tcgen05", ("omni_tc5.cu",)), ("tc", ("omni_tc.cu",)),
+_PASS_SOURCES = [("lagsum-tcgen05", ("omni_xspec5.cu",)), ("xspec-tcgen05", ("omni_xspec5.cu",)),
+                 ("xspec", ("omni_tiles.cu",)), ("tcgen05", ("omni_tc5.cu",)), ("tc", ("omni_tc.cu",)),
                  ("level", ("omni_fft_level.cuh", "omni_fft_level_a.cu", "omni_fft_level_b.cu")),
                  ("smem", ("omni_fft_smem.cuh", "omni_fft_smem_a.cu", "omni_fft_smem_b.cu",
                            "omni_fft_smem_c.cu")),
@@ -218,8 +219,11 @@ def units_per_launch(stat, profiled_units):
     return profiled_units / max(1, stat["launches"])
 
 
-def roofline(stats, workload, path_precision, profiled_units=0, serial_shares=None):
-    """Roofline of the dominant kernel (largest share of the event-timed region)."""
+def roofline(stats, workload, path_precision, profiled_units=0, serial_shares=None, serial_stats=None):
+    """Roofline of the dominant kernel (largest share of the event-timed region).
+    serial_stats: the same kernels timed with the two-stream chunk overlap off,
+    where a launch's event span is that kernel alone (reported beside the main
+    figure, which comes from the headline's own configuration)."""
     timed = [s for s in stats if s["launches"] > 0 and s["total_ms"] > 0]
     if not timed:
         return None
@@ -252,13 +256,44 @@ def roofline(stats, workload, path_precision, profiled_units=0, serial_shares=No
                 "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 x max SM clock"}
     traffic, traffic_note = recorded_traffic(top["name"], workload, path_precision,
                                              units_per_launch(top, profiled_units))
+    serial = None
+    for st in serial_stats or []:
+        if st["name"] == top["name"] and st["launches"] > 0 and st["total_ms"] > 0:
+            s_avg = st["total_ms"] / st["launches"] * 1e-3
+            s_b, s_f = st["bytes"] / st["launches"], st["flops"] / st["launches"]
+            peak = main["peak"]
+            serial = {"avg_launch_ms": s_avg * 1e3, "achieved": round(s_f / s_avg / 1e12, 2),
+                      "frac": round(s_f / s_avg / 1e12 / peak, 4),
+                      "hbm_achieved": round(s_b / s_avg / 1e9, 1),
+                      "hbm_frac": round(s_b / s_avg / 1e9 / hbm_peak, 4)}
     main.update({"traffic": traffic, "traffic_note": traffic_note,
                  "kernel": top["name"], "flops_per_launch": flops_per_launch,
                  "avg_launch_ms": avg_s * 1e3,
                  "share_of_kernel_time": round(top["total_ms"] / total, 4),
                  "share_serial": (serial_shares or {}).get(top["name"]),
-                 "hbm": hbm})
+                 "hbm": hbm, "serial": serial})
     return main
+
+
+def step_hbm(stats, ms_per_step):
+    """Algorithmic bytes of every pass of one step (from the profiled steps) over
+    the step time: the step-level fraction of the HBM roofline."""
+    timed = [s for s in stats if s["launches"] > 0]
+    if not timed or not ms_per_step:
+        return None
+    peaks = {}
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            peaks = json.load(f)
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    per_step = sum(s["bytes"] for s in timed) / PROFILED_STEPS
+    gbs = per_step / (ms_per_step * 1e-3) / 1e9
+    return {"bytes_per_step": per_step, "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+            "frac": round(gbs / hbm_peak, 4),
+            "note": "algorithmic bytes (voltages in, spectra out and back in, accumulator folds) "
+                    "of all passes per step / ms_per_step; peak %s" %
+                    ("of measured" if peaks else "of fallback")}
 
 
 # ------------------------------------------------------------------ CPU oracle
@@ -575,6 +610,8 @@ def run_ours(args):
     # concurrent kernels overlap, so the headline run's shares are not serial
     # shares; these are the ones an ncu launch list, serialised, can confirm)
     serial = None
+    sstats = None
+    serial_ms = None
     if rank == 0:
         os.environ["OMNI_OVERLAP"] = "0"
         try:
@@ -582,7 +619,7 @@ def run_ours(args):
         finally:
             del os.environ["OMNI_OVERLAP"]
         svis = torch.empty_like(vis)
-        _, sstats = timed_steps(sp, x, svis, 2, 3, stream, lambda: None, True)
+        serial_ms, sstats = timed_steps(sp, x, svis, 2, 3, stream, lambda: None, True)
         sp.close()
         del svis
         tot = sum(st["total_ms"] for st in sstats if st["launches"])
@@ -753,7 +790,9 @@ def run_ours(args):
                            "per-launch events off; roofline and kernels from %d further steps "
                            "with per-launch CUDA events" % PROFILED_STEPS),
                 "roofline": roofline(stats, args.workload, args.precision, head["prof_units"],
-                                     serial),
+                                     serial, sstats),
+                "step_hbm": step_hbm(stats, head["ms"]),
+                "serial_profiled_ms_per_step": serial_ms,
                 "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": stats[0]["timed_launches"] if stats else 0,
                 "clocks": clocks, "epilogue": epilogue, "direct_n2": n2, "beam_space": beams,
