@@ -68,9 +68,22 @@ typedef enum omni_dtype {
     OMNI_IN_CI8 = 1    /* int8 re, int8 im (2 bytes), values in [-127, 127] */
 } omni_dtype;
 
+/* Mixed precision (2-level hierarchies and tile plans): the coarse level is
+ * evaluated in lag space (Sec. II.D's convolution over the level-2 axes as a
+ * sum over level-1 block pairs of equal grid offset): per level-1 frequency, the
+ * blocks' cross-spectra summed over time as one tensor-core GEMM with the
+ * samples as the contraction axis, FP32 accumulation, FP64 fold per chunk.
+ * Level 1 runs as split-FP16 DFT-GEMMs (int8 voltages, 16x16 blocks, FP16
+ * precision) or as the FP32 FFT.  Both mixed forms keep relative errors near
+ * 1e-6 against the FP64 oracle. */
 typedef enum omni_precision {
-    OMNI_FP32 = 0,       /* all FFT arithmetic in FP32 */
-    OMNI_MIXED_FP16 = 1  /* DFT stages as split FP16 tensor-core GEMMs */
+    OMNI_FP32 = 0,        /* all FFT arithmetic in FP32 */
+    OMNI_MIXED_FP16 = 1,  /* GEMM operands split in two FP16 halves (3 products); the
+                           * spectra scaled by a power of two first: fixed from the
+                           * block size for int8 voltages, per channel and chunk from
+                           * the voltages' max |re|, |im| for float voltages */
+    OMNI_MIXED_BF16 = 2   /* GEMM operands split in three BF16 parts (6 products, about
+                           * 24 bits, FP32's range: no scaling) */
 } omni_precision;
 
 typedef struct omni_plan omni_plan;
@@ -94,10 +107,15 @@ omni_status omni_baselines(const omni_level* levels, int n_levels, int32_t* dm,
 
 /* Create a plan on the current CUDA device for C channels of voltages of the
  * given type.  The plan owns its device accumulator ([C][L] FP64, L =
- * prod L_d), scratch buffers and staging memory; all are allocated here.
+ * prod L_d; mixed plans [C][L1 L2 of level 1][(2 n3 - 1)(2 n4 - 1)] complex),
+ * scratch buffers and staging memory; all are allocated here.  The samples of
+ * each omni_correlate call are processed in chunks the plan sizes itself (from
+ * its buffer target, the kernels' occupancy and, for mixed plans, whole waves
+ * of CTAs); results do not depend on the chunking.
  * Errors: INVALID_ARG, COLLISION, UNSUPPORTED (more than 8 levels, a padded
- * axis longer than 4096, or a non-power-of-two padded axis longer than 1024),
- * OOM, CUDA. */
+ * axis longer than 4096, or a non-power-of-two padded axis longer than 1024;
+ * mixed precision outside 2-level hierarchies of at most 64 level-1 blocks
+ * whose padded level-1 size 4 n1 n2 is a multiple of 4), OOM, CUDA. */
 omni_status omni_plan_create(const omni_level* levels, int n_levels, int64_t n_channels,
                              omni_dtype dtype, omni_precision precision, omni_plan** out);
 
@@ -152,9 +170,9 @@ omni_status omni_plan_create_beams(const omni_level* levels, int n_levels, int64
  * ([C][4 n1 n2][n_tiles][n_tiles] on the mixed path, transposed once per
  * omni_visibilities call into the plan's scratch before the inverse).
  * precision OMNI_FP32: the cross-spectra are summed on CUDA cores in FP32;
- * OMNI_MIXED_FP16: per tile frequency they are one tensor-core GEMM over the
- * samples (tcgen05, FP16 hi/lo split, FP32 accumulation in tensor memory),
- * for int8 voltages, at most 64 tiles and 4 n1 n2 a multiple of 4.
+ * OMNI_MIXED_FP16 / _BF16: per tile frequency they are one tensor-core GEMM over
+ * the samples (tcgen05, operands split as the precision says, FP32 accumulation
+ * in tensor memory), for at most 64 tiles and 4 n1 n2 a multiple of 4.
  * Errors: as omni_plan_create; INVALID_ARG for n_tiles < 1 or a NULL or
  * non-finite offset; UNSUPPORTED beyond 4096 tiles or outside the mixed
  * path's limits; COLLISION if two antennas of different tiles coincide. */
@@ -222,7 +240,7 @@ omni_status omni_plan_info(const omni_plan* plan, int* n_dims, int32_t* dims,
  * time; Appendix A steps 3-5).  volts_dev: DEVICE pointer to [C][T][N]
  * complex voltages of the plan's dtype, owned by the caller and only read,
  * aligned to its element size (2 bytes for int8, 8 for float32; 16 bytes for
- * mixed-precision plans).  T >= 0 (T = 0 is a no-op).  Asynchronous on stream. */
+ * mixed-precision plans whose level 1 runs on tensor cores: int8 16x16 blocks).  T >= 0 (T = 0 is a no-op).  Asynchronous on stream. */
 omni_status omni_correlate(omni_plan* plan, const void* volts_dev, int64_t T, void* stream);
 
 /* Same as omni_correlate for voltages in HOST memory (pageable or pinned):

@@ -254,6 +254,7 @@ struct omni_plan {
     int64_t fwd_elems = 0;    // float2 per sample, largest non-final forward output
     int64_t inv_elems = 0;    // float2 per channel, largest non-final inverse output
     float2* buf[2] = {nullptr, nullptr};
+    float* chan_max = nullptr;  // FP16 plans of float voltages: per chunk channel max |x|, two chunk slots
     int64_t buf_elems = 0;
     double* P = nullptr;      // [C][L]
     int* dev_err = nullptr;   // device error word of bounded waits
@@ -379,9 +380,13 @@ omni_status build_passes(omni_plan* pl) {
     }
     pl->fwd.clear();
     pl->fwd_elems = 0;
-    if (pl->precision == OMNI_MIXED_FP16 && !pl->n_tiles) {
-        // tensor-core stages: level 1 (16x16 -> 32x32 per block), level 2 (8x8 -> 16x16) + |F|^2
-        stages.clear();
+    if (pl->precision != OMNI_FP32 && !pl->n_tiles) {
+        const bool tc_shape = pl->precision == OMNI_MIXED_FP16 && tc_supports(g.n, g.D, pl->dtype == OMNI_IN_CI8);
+        // level 1 on tensor cores (mma.sync split-FP16 DFT-GEMMs) for int8 16x16 blocks,
+        // else the FP32 level-1 FFT; level 2 in lag space (tcgen05) unless the knob asks
+        // for the per-sample DFT-GEMM forms, which exist for the 16x16-on-8x8 shape only
+        const bool tc_a = tc_shape && pl->knobs.tc_stage_a;
+        const bool lag = pl->knobs.lag_sum || !tc_shape;
         Pass pa{};
         pa.axis = 0;
         pa.kind = KIND_TC_A;
@@ -391,32 +396,43 @@ omni_status build_passes(omni_plan* pl) {
         pa.q_out = g.Lp[0] * g.Lp[1];
         pa.inner = 1;
         pa.outer = (int64_t)g.n[2] * g.n[3];
+        if (!tc_a && !lag) choose_level(pa);
+        std::vector<Pass> level1;
+        if (tc_a || !lag) {
+            level1.push_back(pa);
+        } else {
+            // the generic level-1 passes (a level pass, or one pass per axis), MID mode,
+            // leaving [block][L0 L1] per sample for the lag-sum pass
+            for (const auto& stg : stages) {
+                if (stg.first >= 2) continue;
+                const int d = stg.first, last_axis = stg.second ? d + 1 : d;
+                Pass q{};
+                q.axis = d;
+                q.L = g.Lp[d];
+                q.n = g.n[d];
+                q.q_out = stg.second ? g.Lp[d] * g.Lp[d] : g.Lp[d];
+                q.inner = 1;
+                q.outer = 1;
+                for (int e = 0; e < d; ++e) q.inner *= g.Lp[e];
+                for (int e = last_axis + 1; e < g.D; ++e) q.outer *= g.n[e];
+                q.mode = MODE_MID;
+                if (stg.second) {
+                    choose_level(q);
+                } else {
+                    choose_kind(q);
+                    if (q.n == q.L && q.L > 1 && q.kind == KIND_SMEM) q.kind = KIND_DIRECT;
+                }
+                level1.push_back(q);
+            }
+        }
+        stages.clear();
         Pass pb{};
         pb.axis = 2;
-        // warp-level mma.sync by default (measured faster for these 16-point
-        // DFTs); OMNI_TCGEN05=1 selects the tensor-memory (tcgen05) variant
-        pb.kind = KIND_TC_B;
-        if (const char* env = std::getenv("OMNI_TCGEN05"))
-            if (std::atoi(env) != 0) pb.kind = KIND_TC5_B;
         pb.mode = MODE_LAST;
-        pb.L = g.Lp[2];
-        pb.n = g.n[2];
-        pb.q_out = g.Lp[2] * g.Lp[3];
-        pb.inner = (int64_t)g.Lp[0] * g.Lp[1];
-        pb.outer = 1;
-        pb.W = pb.kind == KIND_TC_B ? tc_stage_b_tile() : tc5_stage_b_tile();
-        if (!pl->knobs.tc_stage_a) {
-            // level 1 as the FP32 FFT on CUDA cores, level 2 on tensor cores: the two
-            // passes of consecutive chunks then load different pipes
-            pa.L = g.Lp[0];
-            pa.n = g.n[0];
-            choose_level(pa);
-            pb.unscaled_in = 1;
-        }
-        if (pl->knobs.lag_sum) {
-            // level 2 in lag space: per level-1 frequency the 64 x 64 block
-            // cross-spectra summed over the chunk's samples (one tcgen05 GEMM with
-            // the samples as K), then summed over block pairs of equal grid offset
+        if (lag) {
+            // level 2 in lag space: per level-1 frequency the block cross-spectra
+            // summed over the chunk's samples (one tcgen05 GEMM with the samples as
+            // K), then summed over block pairs of equal grid offset
             pb.kind = KIND_COV5;
             pb.L = g.Lp[0] * g.Lp[1];
             pb.n = g.n[2] * g.n[3];
@@ -425,12 +441,37 @@ omni_status build_passes(omni_plan* pl) {
             pb.q_out = pb.L;
             pb.L1 = g.n[2];
             pb.L2 = g.n[3];
-            pb.W = 0;
+            pb.bf16 = pl->precision == OMNI_MIXED_BF16;
+            pb.unscaled_in = tc_a ? 0 : 1;
+            if (!pb.bf16 && !tc_a) {
+                // FP16 operands: a power of two keeps |Y| <= 2^12 (int8: from the block size;
+                // float voltages: per channel from the chunk's max |x|)
+                const int64_t nb = (int64_t)g.n[0] * g.n[1];
+                if (pl->dtype == OMNI_IN_CI8)
+                    pb.scale_e = (int)std::ceil(std::log2((double)nb * 127.0 * 1.41422)) - 12;
+                else
+                    pb.scale_n = (int)nb;
+            }
             pl->lag_pairs = (int64_t)(2 * g.n[2] - 1) * (2 * g.n[3] - 1);
+        } else {
+            // per-sample level-2 DFT-GEMMs + |F|^2: warp-level mma.sync by default,
+            // OMNI_TCGEN05=1 selects the tensor-memory (tcgen05) variant
+            pb.kind = KIND_TC_B;
+            if (const char* env = std::getenv("OMNI_TCGEN05"))
+                if (std::atoi(env) != 0) pb.kind = KIND_TC5_B;
+            pb.L = g.Lp[2];
+            pb.n = g.n[2];
+            pb.q_out = g.Lp[2] * g.Lp[3];
+            pb.inner = (int64_t)g.Lp[0] * g.Lp[1];
+            pb.outer = 1;
+            pb.W = pb.kind == KIND_TC_B ? tc_stage_b_tile() : tc5_stage_b_tile();
+            pb.unscaled_in = tc_a ? 0 : 1;
         }
-        pl->fwd.push_back(pa);
+        for (const Pass& q : level1) {
+            pl->fwd.push_back(q);
+            pl->fwd_elems = std::max(pl->fwd_elems, q.outer * q.q_out * q.inner);
+        }
         pl->fwd.push_back(pb);
-        pl->fwd_elems = pa.outer * pa.q_out;
     }
     for (size_t k = 0; k < stages.size(); ++k) {
         const int d = stages[k].first;
@@ -461,8 +502,16 @@ omni_status build_passes(omni_plan* pl) {
         // tile hybrid: cross-spectra of every tile pair, per frequency of the tile
         Pass x{};
         x.axis = 0;
-        x.kind = pl->precision == OMNI_MIXED_FP16 ? KIND_XSPEC5 : KIND_XSPEC;
+        x.kind = pl->precision != OMNI_FP32 ? KIND_XSPEC5 : KIND_XSPEC;
         x.unscaled_in = 1;  // the tile FFT writes unscaled spectra
+        x.bf16 = pl->precision == OMNI_MIXED_BF16;
+        if (pl->precision == OMNI_MIXED_FP16) {
+            const int64_t nt = (int64_t)g.n[0] * g.n[1];
+            if (pl->dtype == OMNI_IN_CI8)
+                x.scale_e = (int)std::ceil(std::log2((double)nt * 127.0 * 1.41422)) - 12;
+            else
+                x.scale_n = (int)nt;
+        }
         x.mode = MODE_LAST;
         x.L = g.Lp[0] * g.Lp[1];
         x.n = (int)pl->n_tiles;
@@ -609,6 +658,7 @@ void release(omni_plan* pl) {
     if (pl->copy_stream) cudaStreamSynchronize(pl->copy_stream);
     cudaFree(pl->buf[0]);
     cudaFree(pl->buf[1]);
+    cudaFree(pl->chan_max);
     cudaFree(pl->P);
     cudaFree(pl->dev_err);
     cudaFree(pl->vis_tmp);
@@ -768,9 +818,13 @@ omni_status run_chunk(omni_plan* pl, const void* volts, int64_t vc0, int64_t Tsr
     const void* src = volts;
     int src_kind = pl->dtype == OMNI_IN_CI8 ? SRC_CI8 : SRC_CF32;
     int64_t src_stride = 0;
+    // FP16 plans of float voltages: the chunk's per-channel max |x| (one slot per
+    // overlapped chunk), measured before its first pass
+    float* chan_max = pl->chan_max ? pl->chan_max + (slot >= 0 ? slot : 0) * pl->Cc : nullptr;
     for (size_t k = 0; k < pl->fwd.size(); ++k) {
         const Pass& p = pl->fwd[k];
         PassArgs a{};
+        a.chan_max = chan_max;
         a.src = src;
         a.src_kind = src_kind;
         a.src_stride = src_stride;
@@ -791,6 +845,11 @@ omni_status run_chunk(omni_plan* pl, const void* volts, int64_t vc0, int64_t Tsr
             // pass that read this buffer two chunks ago
             launch_stream = pl->aux_stream;
             OMNI_CUDA(cudaStreamWaitEvent(launch_stream, pl->last_done[slot], 0), "cudaStreamWaitEvent");
+        }
+        if (k == 0 && chan_max) {
+            cudaError_t e = launch_chan_absmax(volts, src_kind, vc0, Tsrc, t0, pl->g.N, cc, tc, chan_max,
+                                               launch_stream);
+            if (e != cudaSuccess) return cuda_fail(e, "channel scale launch");
         }
         if (p.mode == MODE_LAST) {
             a.S = cc;
@@ -1127,7 +1186,12 @@ omni_status omni_plan_create_tuned(const omni_level* levels, int n_levels, int64
     std::vector<Knobs> cands;
     for (int64_t mb : {384, 768, 1536, 3072})
         for (int ov : {1, 0}) {
-            if (precision == OMNI_MIXED_FP16) {
+            if (precision == OMNI_MIXED_BF16) {
+                Knobs k;
+                k.chunk_mb = mb;
+                k.overlap = ov;
+                cands.push_back(k);
+            } else if (precision == OMNI_MIXED_FP16) {
                 for (int sa : {0, 1})
                     for (double sp : {0.0, 0.3, 0.6}) {
                         Knobs k;
@@ -1262,14 +1326,12 @@ static omni_status create_plan(const omni_level* levels, int n_levels, int64_t n
     *out = nullptr;
     if (n_channels < 1) return fail(OMNI_ERR_INVALID_ARG, "n_channels must be >= 1");
     if (dtype != OMNI_IN_CF32 && dtype != OMNI_IN_CI8) return fail(OMNI_ERR_INVALID_ARG, "unknown dtype %d", (int)dtype);
-    if (precision != OMNI_FP32 && precision != OMNI_MIXED_FP16)
+    if (precision != OMNI_FP32 && precision != OMNI_MIXED_FP16 && precision != OMNI_MIXED_BF16)
         return fail(OMNI_ERR_INVALID_ARG, "unknown precision %d", (int)precision);
     if (beams && precision != OMNI_FP32)
         return fail(OMNI_ERR_UNSUPPORTED, "beam-space plans run the FP32 path");
     if (beams && levels && n_levels < 2)
         return fail(OMNI_ERR_UNSUPPORTED, "a beam-space plan needs at least two levels");
-    if (n_tiles && precision == OMNI_MIXED_FP16 && dtype != OMNI_IN_CI8)
-        return fail(OMNI_ERR_UNSUPPORTED, "mixed-precision tile-hybrid plans take int8 voltages");
     omni_plan* pl = new omni_plan();
     pl->beams = beams;
     pl->n_tiles = n_tiles;
@@ -1280,18 +1342,20 @@ static omni_status create_plan(const omni_level* levels, int n_levels, int64_t n
         delete pl;
         return st;
     }
-    if (n_tiles && precision == OMNI_MIXED_FP16 &&
+    if (n_tiles && precision != OMNI_FP32 &&
         !xspec5_supports(n_tiles, (int64_t)pl->g.Lp[0] * pl->g.Lp[1])) {
         delete pl;
         return fail(OMNI_ERR_UNSUPPORTED,
                     "mixed-precision tile-hybrid plans support at most 64 tiles whose padded "
                     "lattice size is a multiple of 4");
     }
-    if (!n_tiles && precision == OMNI_MIXED_FP16 && !tc_supports(pl->g.n, pl->g.D, dtype == OMNI_IN_CI8)) {
+    if (!n_tiles && precision != OMNI_FP32 &&
+        !(pl->g.D == 4 && (int64_t)pl->g.n[2] * pl->g.n[3] <= 64 &&
+          xspec5_supports((int64_t)pl->g.n[2] * pl->g.n[3], (int64_t)pl->g.Lp[0] * pl->g.Lp[1]))) {
         delete pl;
         return fail(OMNI_ERR_UNSUPPORTED,
-                    "the mixed-precision path supports int8 voltages on a 2-level hierarchy of "
-                    "16x16 blocks on an 8x8 grid");
+                    "the mixed-precision path supports 2-level hierarchies of at most 64 level-1 "
+                    "blocks whose padded level-1 lattice size is a multiple of 4");
     }
     pl->C = n_channels;
     pl->dtype = dtype;
@@ -1378,6 +1442,12 @@ static omni_status create_plan(const omni_level* levels, int n_levels, int64_t n
     init_stats(pl);
     const size_t buf_bytes = (size_t)std::max<int64_t>(1, pl->buf_elems) * sizeof(float2);
     const size_t P_bytes = (size_t)pl->C * acc_doubles(pl) * sizeof(double);
+    bool data_scale = false;
+    for (const Pass& q : pl->fwd) data_scale = data_scale || (q.scale_n > 0 && !q.bf16);
+    if (data_scale && (e = cudaMalloc(&pl->chan_max, (size_t)2 * pl->Cc * sizeof(float))) != cudaSuccess) {
+        release(pl);
+        return cuda_fail(e, "cudaMalloc");
+    }
     if ((e = cudaMalloc(&pl->buf[0], buf_bytes)) != cudaSuccess ||
         (e = cudaMalloc(&pl->buf[1], buf_bytes)) != cudaSuccess ||
         (e = cudaMalloc(&pl->P, P_bytes)) != cudaSuccess ||
@@ -1505,7 +1575,7 @@ omni_status omni_correlate(omni_plan* pl, const void* volts_dev, int64_t T, void
     if (!volts_dev) return fail(OMNI_ERR_INVALID_ARG, "volts_dev is NULL");
     if ((uintptr_t)volts_dev % elem_bytes(pl->dtype) != 0)
         return fail(OMNI_ERR_INVALID_ARG, "volts_dev must be aligned to its element size");
-    if (pl->precision == OMNI_MIXED_FP16 && (uintptr_t)volts_dev % 16 != 0)
+    if (pl->fwd.front().kind == KIND_TC_A && (uintptr_t)volts_dev % 16 != 0)
         return fail(OMNI_ERR_INVALID_ARG, "mixed-precision plans need 16-byte aligned volts_dev");
     DeviceGuard dg(pl->device);
     cudaStream_t s = (cudaStream_t)stream;

@@ -57,7 +57,11 @@ struct Pass {
     int L1, L2;     // KIND_SMEM split
     int W;          // KIND_SMEM / KIND_LEVEL: consecutive inner indices per unit
     int grid_cap;   // KIND_LEVEL finest MID: CTAs of the persistent kernel (0 = not used)
-    int unscaled_in;  // KIND_TC_B: level-1 spectra from the FP32 pass, not pre-scaled by 1/16
+    int unscaled_in;  // KIND_TC_B/COV5/XSPEC5: level-1 spectra from the FP32 pass, not pre-scaled by 1/16
+    int bf16;         // KIND_COV5/XSPEC5: BF16 operands split three ways (else FP16 split two ways)
+    int scale_e;      // KIND_COV5/XSPEC5, FP16: the spectra are multiplied by 2^-scale_e before the split
+    int scale_n;      // ... or, when > 0, by a power of two per channel from PassArgs::chan_max
+                      //     (scale_n = antennas per block or tile, bounding |Y| by scale_n max|x| sqrt 2)
     int64_t inner, outer;
     const float2* tw;  // KIND_DIRECT: w_L^m = exp(-2 pi i m / L), m < L
 };
@@ -82,6 +86,7 @@ struct PassArgs {
     int* err;            // device error word (bounded waits that expired set it to 1)
     int force_expire;    // test hook: make the first bounded wait expire
     double fold_scale;   // FP32 LAST passes: factor on the FP64 fold (0 means 1)
+    const float* chan_max;  // per chunk channel: max |re|, |im| of its voltages (KIND_COV5/XSPEC5 with scale_n)
 };
 
 // Upload the twiddle tables to the current device (once per device).
@@ -120,6 +125,10 @@ bool xspec5_supports(int64_t n_tiles, int64_t K);  // <= 64 tiles, K a multiple 
 cudaError_t launch_xspec5(const Pass& p, const PassArgs& a, cudaStream_t stream);
 cudaError_t xspec5_occupancy(int* blocks_per_sm);
 int64_t xspec5_ctas_per_channel(const Pass& p);
+// Per channel of a chunk: max over its voltages of |re| and |im| (out[cc] zeroed
+// first; non-negative floats compared as integers).  src_kind SRC_CF32 or SRC_CI8.
+cudaError_t launch_chan_absmax(const void* volts, int src_kind, int64_t vc0, int64_t T, int64_t t0, int64_t N,
+                               int64_t cc, int64_t tc, float* out, cudaStream_t stream);
 // An accumulator [cv channels from P][K][NP] complex FP64 (NP tile pairs or
 // coarse lags) transposed to [NP][K] in dst (the inverse passes' source layout).
 cudaError_t launch_xspec5_transpose(const double* P, int64_t P_stride, int64_t cv, int64_t K, int64_t NP,

@@ -9,10 +9,14 @@
 // so the (N/M)^2 term of Sec. III is a real GEMM D[m][n] = sum_t X[m][t] X[n][t]
 // with M = N = 128 and K = the chunk's samples, accumulated in tensor memory.
 // X is split into FP16 hi + lo and each group of 16 samples adds three
-// products, hi.hi^T + hi.lo^T + lo.hi^T (about 22 bits, FP32 accumulation).
-// Scaling: the tile spectra are multiplied by 1/16 before the split (|Y| <=
-// 256 x 127 x sqrt 2 for int8 voltages stays inside FP16) and the FP64 fold
-// multiplies by 256.
+// products, hi.hi^T + hi.lo^T + lo.hi^T (about 22 bits, FP32 accumulation), or
+// (BF16) into h + m + l with six products, hh + hm + mh + hl + lh + mm (about 24
+// bits; BF16 has FP32's exponent range, so no scaling).
+// FP16 scaling: the spectra are multiplied by a power of two 2^-e before the
+// split so that |Y| 2^-e <= 2^12 (|Y| <= antennas per block x max|x| x sqrt 2):
+// e fixed from the block size for int8 voltages, or per channel from the
+// chunk's measured max |x| for float voltages; the FP64 fold multiplies by
+// 2^(2e) (and by 256 more when the level-1 pass already scaled by 1/16).
 //
 // CTA = (channel of the chunk, 4 consecutive frequencies); 512 tensor-memory
 // columns hold the 4 accumulators, one CTA per SM.  Warp 9 brings each step's
@@ -32,6 +36,7 @@
 #include "omni_fft_common.cuh"
 
 #include <cuda.h>            // CUtensorMap; the encoder is fetched from the driver at run time
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cudaTypedefs.h>
 
@@ -46,11 +51,18 @@ constexpr int kXF = 4;            // frequencies per CTA (32-byte load runs)
 constexpr int kXT = 64;           // most tiles (2 x 64 = 128 GEMM rows)
 constexpr int kXThreads = 320;    // warps 0-7 convert / epilogue, warp 8 MMA issue, warp 9 TMA
 constexpr int kXProducers = 256;
-constexpr int kXStages = 3;       // shared-memory operand stages
 constexpr int kLBO = 128;         // bytes between K-adjacent core matrices (dense, 128-byte aligned)
 constexpr int kSBO = 256;         // bytes between 8-row groups
-constexpr int kTileBytes = 16 * kSBO;                 // 128 rows x 16 samples, FP16
-constexpr int kStageBytes = kXF * 2 * kTileBytes;     // per frequency: hi, lo
+constexpr int kTileBytes = 16 * kSBO;                 // 128 rows x 16 samples, 16-bit
+// operand stages: FP16 three of hi, lo per frequency; BF16 two of h, m, l
+constexpr int kStageRing = 3 * kXF * 2 * kTileBytes;  // 96 KB either way
+template <int PREC> struct Prec {
+    static constexpr int parts = PREC ? 3 : 2;
+    static constexpr int stages = PREC ? 2 : 3;
+    static constexpr int stage_bytes = kXF * parts * kTileBytes;
+    static_assert(stages * stage_bytes == kStageRing, "operand ring size");
+};
+constexpr int kXStagesMax = 3;
 // raw spectra brought in by the tensor-memory-access unit, kXRaw steps in
 // flight: per step one box of the spectra [sample][tile][K], 16 samples x 64
 // tiles x 4 frequencies x (re, im) FP32 (32-byte rows), landing as
@@ -63,17 +75,17 @@ constexpr int kEp = 68;                               // floats per row (conflic
 constexpr int kEpMat = 64 * kEp;                      // floats per matrix
 constexpr int kMaxU = 960;                            // partial sums per frequency (8 x 8 grid: 8 x 8 x 15)
 constexpr int kMaxQ2 = 225;                           // coarse lags of at most 64 blocks (8 x 8: 15 x 15)
-static_assert(kXF * 2 * kEpMat * 4 + kXF * (kMaxU + kMaxQ2) * 8 <= kXStages * kStageBytes + kXRaw * kRawBytes,
+static_assert(kXF * 2 * kEpMat * 4 + kXF * (kMaxU + kMaxQ2) * 8 <= kStageRing + kXRaw * kRawBytes,
               "epilogue staging fits the pipeline buffers");
 // more than half of an SM's shared memory (one CTA per SM, so that two CTAs
 // never ask for 512 tensor-memory columns on the same SM)
-constexpr size_t kXSmem = (size_t)kXStages * kStageBytes + (size_t)kXRaw * kRawBytes + 1024;
+constexpr size_t kXSmem = (size_t)kStageRing + (size_t)kXRaw * kRawBytes + 1024;
 static_assert(kXSmem > 114 * 1024 && kXSmem <= 227 * 1024, "one CTA per SM");
 constexpr uint32_t kTmemCols = 512;
-constexpr float kXScale = 1.0f / 16.0f;
-constexpr double kXFold = 256.0;
-// kind::f16, FP32 accumulate, FP16 A and B, K-major, M = 128, N = 128
+constexpr int kXScaleTarget = 12;  // FP16: |Y| 2^-e <= 2^12
+// kind::f16, FP32 accumulate, K-major, M = 128, N = 128; A and B FP16 or (bits 7, 10) BF16
 constexpr uint32_t kIdesc128 = (1u << 4) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+constexpr uint32_t kIdesc128Bf16 = kIdesc128 | (1u << 7) | (1u << 10);
 constexpr long long kWaitCycles = 4000000000LL;   // ~2 s
 
 __host__ __device__ inline int tile_off(int row, int k) {
@@ -85,10 +97,10 @@ __device__ __forceinline__ uint64_t sdesc(const void* p) {
     return (uint64_t)((a >> 4) & 0x3FFF) | ((uint64_t)(kLBO >> 4) << 16) |
            ((uint64_t)(kSBO >> 4) << 32) | ((uint64_t)1 << 46);
 }
-__device__ __forceinline__ void mma_ss(uint32_t d, uint64_t a, uint64_t b, int acc) {
+__device__ __forceinline__ void mma_ss(uint32_t d, uint64_t a, uint64_t b, int acc, uint32_t idesc) {
     asm volatile("{\n .reg .pred p, e;\n setp.ne.b32 p, %3, 0;\n elect.sync _|e, 0xffffffff;\n"
                  " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %4, p;\n}\n"
-                 :: "r"(d), "l"(a), "l"(b), "r"(acc), "r"(kIdesc128));
+                 :: "r"(d), "l"(a), "l"(b), "r"(acc), "r"(idesc));
 }
 __device__ __forceinline__ void commit(uint64_t* bar) {
     asm volatile("{\n .reg .pred e;\n elect.sync _|e, 0xffffffff;\n"
@@ -147,6 +159,22 @@ __device__ __forceinline__ void split2(float x0, float x1, uint32_t& hi, uint32_
     hi = h2u(h);
     lo = h2u(__floats2half2_rn(x0 - hf.x, x1 - hf.y));
 }
+__device__ __forceinline__ uint32_t b2u(__nv_bfloat162 h) {
+    uint32_t u;
+    memcpy(&u, &h, 4);
+    return u;
+}
+// (x0, x1) -> h = bf16(x), m = bf16(x - h), l = bf16(x - h - m)
+__device__ __forceinline__ void split3(float x0, float x1, uint32_t& h, uint32_t& m, uint32_t& l) {
+    const __nv_bfloat162 bh = __floats2bfloat162_rn(x0, x1);
+    const float2 fh = __bfloat1622float2(bh);
+    const float r0 = x0 - fh.x, r1 = x1 - fh.y;
+    const __nv_bfloat162 bm = __floats2bfloat162_rn(r0, r1);
+    const float2 fm = __bfloat1622float2(bm);
+    h = b2u(bh);
+    m = b2u(bm);
+    l = b2u(__floats2bfloat162_rn(r0 - fm.x, r1 - fm.y));
+}
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(smem_u32(bar)), "r"(bytes));
 }
@@ -174,12 +202,26 @@ __device__ __forceinline__ void tc_after_sync() { asm volatile("tcgen05.fence::a
 // correlation (Eq. ProofEq2 over the level-2 axes) done in lag space.
 enum { EPI_PAIRS = 0, EPI_LAGS = 1 };
 
-template <int EPI>
+// The power of two 2^-e applied to channel cc's spectra before the FP16 split, and
+// the fold factor that undoes it (and the level-1 pass's own 1/16, if any).
+__device__ __forceinline__ int scale_exp(const Pass& p, const PassArgs& a, int64_t cc) {
+    if (p.bf16) return 0;
+    if (p.scale_n <= 0) return p.scale_e;
+    const float m = a.chan_max[cc];
+    if (!(m > 0.f)) return 0;
+    // smallest e with scale_n m sqrt 2 2^-e <= 2^12 (clamped before the conversion: m may be inf)
+    const float v = ceilf(log2f((float)p.scale_n * m * 1.41422f)) - (float)kXScaleTarget;
+    return v >= 100.f ? 100 : (v <= -100.f ? -100 : (int)v);
+}
+
+template <int EPI, int PREC>
 __global__ void __launch_bounds__(kXThreads, 1) xspec5(Pass p, PassArgs a, const __grid_constant__ CUtensorMap tmap) {
+    using PR = Prec<PREC>;
+    constexpr int kXStages = PR::stages, kStageBytes = PR::stage_bytes, kParts = PR::parts;
     extern __shared__ unsigned char dsm_raw[];
     // operand stages, 1024-byte aligned
     unsigned char* dsm = reinterpret_cast<unsigned char*>(((uintptr_t)dsm_raw + 1023) & ~(uintptr_t)1023);
-    __shared__ __align__(8) uint64_t full[kXStages], empty[kXStages], done, raw_full[kXRaw], raw_empty[kXRaw];
+    __shared__ __align__(8) uint64_t full[kXStagesMax], empty[kXStagesMax], done, raw_full[kXRaw], raw_empty[kXRaw];
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
 
@@ -191,6 +233,8 @@ __global__ void __launch_bounds__(kXThreads, 1) xspec5(Pass p, PassArgs a, const
     const int64_t k0 = (blockIdx.x - cc * groups) * kXF;
     const int tc = a.tc;
     const int steps = (tc + 15) / 16;
+    const int e_scale = scale_exp(p, a, cc);
+    const double fold = ldexp(1.0, 2 * e_scale) * (p.unscaled_in || p.bf16 ? 1.0 : 256.0);
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
@@ -225,10 +269,8 @@ __global__ void __launch_bounds__(kXThreads, 1) xspec5(Pass p, PassArgs a, const
         // runs on into the next channel) count as zero.
         const int j = 16 * (warp & 3) + (tid & 15), g = warp >> 2, fp = (tid >> 4) & 1;
         const bool live = j < NT;
-        // spectra from the FP32 tile FFT get the 1/16 here; the tensor-core first
-        // pass of a hierarchy already wrote them scaled
-        const float in_scale = p.unscaled_in ? kXScale : 1.0f;
-        const unsigned char* raw = dsm + (size_t)kXStages * kStageBytes;
+        const float in_scale = ldexpf(1.0f, -e_scale);
+        const unsigned char* raw = dsm + (size_t)kStageRing;
         bool ok = true;
         for (int n = 0; n < steps && ok; ++n) {
             const int st = n % kXStages, rs = n % kXRaw;
@@ -247,21 +289,27 @@ __global__ void __launch_bounds__(kXThreads, 1) xspec5(Pass p, PassArgs a, const
             unsigned char* stage = dsm + (size_t)st * kStageBytes;
 #pragma unroll
             for (int fl = 0; fl < 2; ++fl) {
-                unsigned char* thi = stage + (2 * (2 * fp + fl)) * kTileBytes;
-                unsigned char* tlo = thi + kTileBytes;
+                // the frequency's operand tiles: hi, lo (FP16) or h, m, l (BF16)
+                unsigned char* t0 = stage + (kParts * (2 * fp + fl)) * kTileBytes;
 #pragma unroll
                 for (int part = 0; part < 2; ++part) {  // rows j (re) and 64 + j (im)
-                    uint32_t h[4], l[4];
+                    uint32_t h[4], m[4], l[4];
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
                         const float4 a0 = cur[2 * q], a1 = cur[2 * q + 1];
                         const float x0 = (fl == 0 ? (part == 0 ? a0.x : a0.y) : (part == 0 ? a0.z : a0.w)) * in_scale;
                         const float x1 = (fl == 0 ? (part == 0 ? a1.x : a1.y) : (part == 0 ? a1.z : a1.w)) * in_scale;
-                        split2(x0, x1, h[q], l[q]);
+                        if (PREC) split3(x0, x1, h[q], m[q], l[q]);
+                        else split2(x0, x1, h[q], l[q]);
                     }
                     const int off = tile_off(j + 64 * part, 8 * g);
-                    *reinterpret_cast<uint4*>(thi + off) = make_uint4(h[0], h[1], h[2], h[3]);
-                    *reinterpret_cast<uint4*>(tlo + off) = make_uint4(l[0], l[1], l[2], l[3]);
+                    *reinterpret_cast<uint4*>(t0 + off) = make_uint4(h[0], h[1], h[2], h[3]);
+                    if (PREC) {
+                        *reinterpret_cast<uint4*>(t0 + kTileBytes + off) = make_uint4(m[0], m[1], m[2], m[3]);
+                        *reinterpret_cast<uint4*>(t0 + 2 * kTileBytes + off) = make_uint4(l[0], l[1], l[2], l[3]);
+                    } else {
+                        *reinterpret_cast<uint4*>(t0 + kTileBytes + off) = make_uint4(l[0], l[1], l[2], l[3]);
+                    }
                 }
             }
             // the raw values have been consumed (split and stored) and the operand
@@ -282,7 +330,7 @@ __global__ void __launch_bounds__(kXThreads, 1) xspec5(Pass p, PassArgs a, const
             const int rs = n % kXRaw;
             if (n >= kXRaw) ok = __all_sync(0xffffffffu, wait_bar(&raw_empty[rs], (n / kXRaw - 1) & 1));
             if (!ok) break;
-            unsigned char* slot = dsm + (size_t)kXStages * kStageBytes + (size_t)rs * kRawBytes;
+            unsigned char* slot = dsm + (size_t)kStageRing + (size_t)rs * kRawBytes;
             if (elect_one()) {
                 mbar_expect_tx(&raw_full[rs], box_bytes);
                 tma_load3(slot, &tmap, (int)(2 * k0), 0, (int)(cc * tc + 16 * n), &raw_full[rs]);
@@ -296,7 +344,7 @@ __global__ void __launch_bounds__(kXThreads, 1) xspec5(Pass p, PassArgs a, const
             if (!wait_bar(&raw_full[n % kXRaw], (n / kXRaw) & 1)) ok = false;
         if (!__all_sync(0xffffffffu, ok)) atomicExch(&abort_flag, 1);
     } else {
-        // ---- warp 8: MMA issue, per stage 3 products per frequency
+        // ---- warp 8: MMA issue, per stage 3 (FP16) or 6 (BF16) products per frequency
         bool ok = true;
         for (int n = 0; n < steps && ok; ++n) {
             const int st = n % kXStages;
@@ -306,12 +354,24 @@ __global__ void __launch_bounds__(kXThreads, 1) xspec5(Pass p, PassArgs a, const
             unsigned char* stage = dsm + (size_t)st * kStageBytes;
 #pragma unroll
             for (int f = 0; f < kXF; ++f) {
-                const uint64_t hi = sdesc(stage + (2 * f) * kTileBytes);
-                const uint64_t lo = sdesc(stage + (2 * f + 1) * kTileBytes);
                 const uint32_t d = tmem + 128 * f;
-                mma_ss(d, hi, hi, n > 0);   // hi hi^T
-                mma_ss(d, hi, lo, 1);       // hi lo^T
-                mma_ss(d, lo, hi, 1);       // lo hi^T
+                if (PREC) {
+                    const uint64_t h = sdesc(stage + (3 * f) * kTileBytes);
+                    const uint64_t m = sdesc(stage + (3 * f + 1) * kTileBytes);
+                    const uint64_t l = sdesc(stage + (3 * f + 2) * kTileBytes);
+                    mma_ss(d, h, h, n > 0, kIdesc128Bf16);
+                    mma_ss(d, h, m, 1, kIdesc128Bf16);
+                    mma_ss(d, m, h, 1, kIdesc128Bf16);
+                    mma_ss(d, h, l, 1, kIdesc128Bf16);
+                    mma_ss(d, l, h, 1, kIdesc128Bf16);
+                    mma_ss(d, m, m, 1, kIdesc128Bf16);
+                } else {
+                    const uint64_t hi = sdesc(stage + (2 * f) * kTileBytes);
+                    const uint64_t lo = sdesc(stage + (2 * f + 1) * kTileBytes);
+                    mma_ss(d, hi, hi, n > 0, kIdesc128);   // hi hi^T
+                    mma_ss(d, hi, lo, 1, kIdesc128);       // hi lo^T
+                    mma_ss(d, lo, hi, 1, kIdesc128);       // lo hi^T
+                }
             }
             commit(&empty[st]);
         }
@@ -397,8 +457,8 @@ __global__ void __launch_bounds__(kXThreads, 1) xspec5(Pass p, PassArgs a, const
                         for (int u = 0; u < kIB; ++u) {
                             const int ii = i0 + 4 * u;
                             if (ii < NT) {
-                                cur[u].x += kXFold * (double)re[ii * kEp + jj];
-                                cur[u].y += kXFold * (double)im[ii * kEp + jj];
+                                cur[u].x += fold * (double)re[ii * kEp + jj];
+                                cur[u].y += fold * (double)im[ii * kEp + jj];
                                 col[(int64_t)ii * NT] = cur[u];
                             }
                         }
@@ -496,8 +556,8 @@ __global__ void __launch_bounds__(kXThreads, 1) xspec5(Pass p, PassArgs a, const
                 const int e = tid + kXProducers * m;
                 if (warp < 8 && e < kXF * Q2) {
                     double2 r = pre[m];
-                    r.x += kXFold * (double)R[e].x;
-                    r.y += kXFold * (double)R[e].y;
+                    r.x += fold * (double)R[e].x;
+                    r.y += fold * (double)R[e].y;
                     S[k0 * Q2 + e] = r;
                 }
             }
@@ -547,9 +607,9 @@ bool xspec5_supports(int64_t n_tiles, int64_t K) { return n_tiles >= 1 && n_tile
 int64_t xspec5_ctas_per_channel(const Pass& p) { return p.L / kXF; }
 
 cudaError_t xspec5_occupancy(int* blocks_per_sm) {
-    cudaError_t e = smem_limit_once((const void*)xspec5<EPI_PAIRS>, kXSmem);
+    cudaError_t e = smem_limit_once((const void*)xspec5<EPI_PAIRS, 0>, kXSmem);
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, xspec5<EPI_PAIRS>, kXThreads, kXSmem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, xspec5<EPI_PAIRS, 0>, kXThreads, kXSmem);
     if (e == cudaSuccess && *blocks_per_sm > 1) *blocks_per_sm = 1;  // 512 tensor-memory columns
     return e;
 }
@@ -587,18 +647,73 @@ cudaError_t launch_xspec5(const Pass& p, const PassArgs& a, cudaStream_t st) {
     CUtensorMap map;
     const cudaError_t me = encode_map(a, p, &map);
     if (me != cudaSuccess) return me;
+    if (p.scale_n > 0 && !p.bf16 && !a.chan_max) return cudaErrorInvalidValue;
+    void (*kern)(Pass, PassArgs, const CUtensorMap) = nullptr;
     if (p.kind == KIND_COV5) {
         if (p.L1 < 1 || p.L2 < 1 || p.L1 * p.L2 != p.outer) return cudaErrorInvalidValue;
         const int na = std::max(p.L1, p.L2), nb = std::min(p.L1, p.L2);
-        if (nb * nb * (2 * na - 1) > kMaxU) return cudaErrorInvalidValue;
-        cudaError_t e = smem_limit_once((const void*)xspec5<EPI_LAGS>, kXSmem);
-        if (e != cudaSuccess) return e;
-        xspec5<EPI_LAGS><<<(unsigned)blocks, kXThreads, kXSmem, st>>>(p, a, map);
-        return cudaGetLastError();
+        if (nb * nb * (2 * na - 1) > kMaxU || (2 * p.L1 - 1) * (2 * p.L2 - 1) > kMaxQ2) return cudaErrorInvalidValue;
+        kern = p.bf16 ? xspec5<EPI_LAGS, 1> : xspec5<EPI_LAGS, 0>;
+    } else {
+        kern = p.bf16 ? xspec5<EPI_PAIRS, 1> : xspec5<EPI_PAIRS, 0>;
     }
-    cudaError_t e = smem_limit_once((const void*)xspec5<EPI_PAIRS>, kXSmem);
+    cudaError_t e = smem_limit_once((const void*)kern, kXSmem);
     if (e != cudaSuccess) return e;
-    xspec5<EPI_PAIRS><<<(unsigned)blocks, kXThreads, kXSmem, st>>>(p, a, map);
+    kern<<<(unsigned)blocks, kXThreads, kXSmem, st>>>(p, a, map);
+    return cudaGetLastError();
+}
+
+namespace {
+// one CTA per (channel, slice of its samples); block max in shared memory, then
+// one atomicMax per CTA on the float's bits (non-negative floats order as integers)
+template <int SRC>
+__global__ void __launch_bounds__(256) chan_absmax(const void* volts, int64_t vc0, int64_t T, int64_t t0, int64_t N,
+                                                   int64_t tc, float* out) {
+    __shared__ float red[8];
+    const int64_t c = blockIdx.y;
+    const int64_t per = tc * N;  // complex values of the channel in the chunk
+    float m = 0.f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < per; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = i / N, n = i - t * N;
+        const int64_t e = ((vc0 + c) * T + t0 + t) * N + n;
+        float re, im;
+        if (SRC == SRC_CI8) {
+            const char2 v = reinterpret_cast<const char2*>(volts)[e];
+            re = (float)v.x;
+            im = (float)v.y;
+        } else {
+            const float2 v = reinterpret_cast<const float2*>(volts)[e];
+            re = v.x;
+            im = v.y;
+        }
+        m = fmaxf(m, fmaxf(fabsf(re), fabsf(im)));
+    }
+    for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        m = threadIdx.x < 8 ? red[threadIdx.x] : 0.f;
+        for (int o = 4; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        // NaN-free by construction of fmaxf; +inf orders above every finite value
+        if (threadIdx.x == 0) atomicMax(reinterpret_cast<int*>(out + c), __float_as_int(m));
+    }
+}
+}  // namespace
+
+cudaError_t launch_chan_absmax(const void* volts, int src_kind, int64_t vc0, int64_t T, int64_t t0, int64_t N,
+                               int64_t cc, int64_t tc, float* out, cudaStream_t st) {
+    if (cc <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(out, 0, (size_t)cc * sizeof(float), st);
+    if (e != cudaSuccess || tc <= 0 || N <= 0) return e;
+    const int64_t per = tc * N;
+    const unsigned bx = (unsigned)std::min<int64_t>(64, (per + 255) / 256);
+    const dim3 grid(bx, (unsigned)cc);
+    if (src_kind == SRC_CI8)
+        chan_absmax<SRC_CI8><<<grid, 256, 0, st>>>(volts, vc0, T, t0, N, tc, out);
+    else if (src_kind == SRC_CF32)
+        chan_absmax<SRC_CF32><<<grid, 256, 0, st>>>(volts, vc0, T, t0, N, tc, out);
+    else
+        return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 

@@ -24,7 +24,7 @@ STATUS_NAMES = {0: "OMNI_OK", 1: "OMNI_ERR_INVALID_ARG", 2: "OMNI_ERR_COLLISION"
                 3: "OMNI_ERR_UNSUPPORTED", 4: "OMNI_ERR_OOM", 5: "OMNI_ERR_CUDA",
                 6: "OMNI_ERR_TIMEOUT"}
 DTYPES = {"cf32": 0, "ci8": 1}
-PRECISIONS = {"fp32": 0, "mixed": 1}
+PRECISIONS = {"fp32": 0, "mixed": 1, "mixed_bf16": 2}
 
 # every entry point include/omni.h declares
 EXPORTS = (

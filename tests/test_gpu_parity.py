@@ -298,11 +298,17 @@ def test_mixed_full_size_sampled():
 
 
 def test_mixed_rejects_unsupported_shapes():
-    with pytest.raises(omni.OmniError) as e:
-        omni.Plan(synth.workload("hier2").levels, 1, dtype="cf32", precision="mixed")
-    assert e.value.status == 3
-    with pytest.raises(omni.OmniError):
-        omni.Plan([synth.Level(16, 16)], 1, dtype="ci8", precision="mixed")
+    """The lag-space mixed path needs exactly two levels, at most 64 level-1 blocks
+    and a padded level-1 lattice whose size is a multiple of 4."""
+    cases = [[synth.Level(16, 16)],                                          # one level
+             synth.hierarchy([(4, 4), (2, 2), (2, 2)], [0, 0.3, 0.6], [0, 0.1, 0]),  # three
+             synth.hierarchy([(4, 4), (9, 8)], [0, 0.4], [0, 0.1]),          # 72 blocks
+             synth.hierarchy([(3, 1), (4, 4)], [0, 0.4], [0, 0.1])]          # 6 x 1 padded
+    for levels in cases:
+        for prec in ("mixed", "mixed_bf16"):
+            with pytest.raises(omni.OmniError) as e:
+                omni.Plan(levels, 1, dtype="ci8", precision=prec)
+            assert e.value.status == 3
 
 
 def test_mixed_tcgen05_variant(monkeypatch):

@@ -199,8 +199,8 @@ def test_tiles_mixed_on_the_lattice_equal_the_hypercube():
 
 def test_tiles_mixed_rejects_what_it_does_not_support():
     tile = synth.Level(4, 4)
-    with pytest.raises(omni.OmniError) as e:      # complex float voltages
-        omni.TilePlan(tile, offsets(3, 9), 1, dtype="cf32", precision="mixed")
+    with pytest.raises(omni.OmniError) as e:      # padded tile size 6 x 1: not a multiple of 4
+        omni.TilePlan(synth.Level(3, 1), offsets(3, 9), 1, dtype="ci8", precision="mixed_bf16")
     assert e.value.status == 3
     with pytest.raises(omni.OmniError) as e:      # more than 64 tiles
         omni.TilePlan(tile, offsets(65, 9, spread=2000.0), 1, dtype="ci8", precision="mixed")
