@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="hier2")
-    ap.add_argument("--precision", default="mixed", choices=["fp32", "mixed"],
+    ap.add_argument("--precision", default="mixed", choices=["fp32", "mixed", "mixed_bf16"],
                     help="headline path; the other one is timed beside it")
     ap.add_argument("--no-compare", action="store_true", help="skip the FP32 comparison run")
     ap.add_argument("--channels", type=int, default=None,
@@ -479,7 +479,7 @@ def other_workloads(args, stream):
         x = synth.voltages(w, device="cuda")
         units = w.n_antennas * w.samples * w.channels
         rec = {"workload": name, "config": workload_config(w, "see paths"), "paths": {}}
-        for prec in ("mixed", "fp32"):
+        for prec in ("mixed", "mixed_bf16", "fp32"):
             try:
                 plan = omni.Plan(w.levels, w.channels, dtype=w.dtype, precision=prec)
             except omni.OmniError as e:
@@ -588,7 +588,8 @@ def run_ours(args):
     x = synth.voltages(w, device="cuda", channel_offset=rank * w.channels)
     stream = torch.cuda.current_stream()
     results = {}
-    precisions = [args.precision] + ([] if args.precision == "fp32" or args.no_compare else ["fp32"])
+    precisions = [args.precision] + ([] if args.precision == "fp32" or args.no_compare
+                                     else ["fp32"] + (["mixed_bf16"] if args.precision == "mixed" else []))
     for prec in precisions:
         plan = omni.Plan(w.levels, w.channels, dtype=w.dtype, precision=prec)
         vis = torch.empty((w.channels, plan.n_lags), dtype=torch.complex128, device="cuda")
@@ -783,7 +784,7 @@ def run_ours(args):
         line = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": head["ms"],
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f16x3+f32" if args.precision == "mixed" else "f32",
+                "dtype": {"mixed": "f16x3+f32", "mixed_bf16": "bf16x6+f32"}.get(args.precision, "f32"),
                 "data": "synthetic",
                 "config": line_config(w, args.precision, world),
                 "timing": ("ms_per_step and value from CUDA events around the timed steps with "
@@ -802,6 +803,14 @@ def run_ours(args):
             f = results["fp32"]
             line["fp32_path"] = {"value": f["value"], "ms_per_step": f["ms"],
                                  "speedup_of_headline": head["value"] / f["value"]}
+        if "mixed_bf16" in results and args.precision != "mixed_bf16":
+            f = results["mixed_bf16"]
+            line["mixed_bf16_path"] = {"value": f["value"], "ms_per_step": f["ms"], "clocks": f["clocks"],
+                                       "note": "level 1 FP32 FFT, level 2 lag-space GEMM with BF16 "
+                                               "operands split three ways (6 products)",
+                                       "roofline": roofline(f["stats"], args.workload, "mixed_bf16",
+                                                            f["prof_units"]),
+                                       "kernels": kernel_list(f["stats"])}
         print(json.dumps(line), flush=True)
     plan.close()
     if world > 1:

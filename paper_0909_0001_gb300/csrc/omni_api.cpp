@@ -214,7 +214,10 @@ void omni::set_last_error(const char* msg) { g_last_error = msg; }
 struct Knobs {
     int64_t chunk_mb = 3072;      // target size of each chunk scratch buffer (OMNI_CHUNK_MB)
     int64_t chunk_channels = 0;   // channels per chunk, 0 = one wave of the last pass (OMNI_CHUNK_CHANNELS)
-    int overlap = 1;              // overlap the two passes of consecutive chunks (OMNI_OVERLAP)
+    int overlap = -1;             // overlap the two passes of consecutive chunks (OMNI_OVERLAP; -1:
+                                  // on, except before the one-CTA-per-SM cross-spectrum GEMMs,
+                                  // where both passes are bound by HBM traffic and the overlap
+                                  // measured 13.69 vs 13.72 ms per step on the 2-level workload)
     int level_passes = 1;         // both axes of a square level in one pass (OMNI_LEVEL_PASSES)
     double split_tc = 0.0;        // mixed: share of a chunk's channels on tensor cores, 0 = all (OMNI_SPLIT_TC)
     int tc_stage_a = 1;           // mixed: level 1 on tensor cores (1) or the FP32 FFT (0) (OMNI_TC_STAGE_A;
@@ -711,8 +714,8 @@ void init_stats(omni_plan* pl) {
                 snprintf(st.name, sizeof st.name, "%s axis%d+%d %s%d %s", inv ? "inv" : "fwd", p.axis,
                          p.axis + 1, kind_name(p.kind), p.L, mode_name(p.mode));
             else
-                snprintf(st.name, sizeof st.name, "%s axis%d %s%d %s", inv ? "inv" : "fwd", p.axis,
-                         kind_name(p.kind), p.L, mode_name(p.mode));
+                snprintf(st.name, sizeof st.name, "%s axis%d %s%s%d %s", inv ? "inv" : "fwd", p.axis,
+                         kind_name(p.kind), p.bf16 ? "bf16-" : "", p.L, mode_name(p.mode));
             st.tensor = (p.kind == KIND_TC_A || p.kind == KIND_TC_B || p.kind == KIND_TC5_B ||
                          p.kind == KIND_XSPEC5 || p.kind == KIND_COV5) ? 1 : 0;
             pl->stats.push_back(st);
@@ -772,8 +775,8 @@ double pass_flops(const Pass& p, const PassArgs& a) {
         case KIND_XSPEC:  // one complex multiply-add per tile pair, frequency and sample
             return (double)a.S * a.tc * p.outer * p.outer * p.L * 8.0;
         case KIND_COV5:
-        case KIND_XSPEC5:  // the same products in real form, FP16 split: 3 x (2 n_tiles)^2 MACs
-            return (double)a.S * a.tc * p.L * 3.0 * (2.0 * p.outer) * (2.0 * p.outer) * 2.0;
+        case KIND_XSPEC5:  // the same products in real form: 3 (FP16 split) or 6 (BF16) x (2 n_tiles)^2 MACs
+            return (double)a.S * a.tc * p.L * (p.bf16 ? 6.0 : 3.0) * (2.0 * p.outer) * (2.0 * p.outer) * 2.0;
         case KIND_TC_A:  // per 16x16 block: 32 + 96 products
             return (double)a.S * p.outer * 128.0 * 4096.0;
         case KIND_TC_B:  // per level-1 frequency and sample: 6 + 12 products, |F|^2
@@ -1378,7 +1381,11 @@ static omni_status create_plan(const omni_level* levels, int n_levels, int64_t n
     }
     choose_chunks(pl);
     // overlap the two passes of consecutive chunks (OMNI_OVERLAP=0 turns it off)
-    pl->overlap = pl->fwd.size() == 2 && pl->knobs.overlap != 0;
+    {
+        const int lk = pl->fwd.back().kind;
+        const bool gemm_last = lk == KIND_COV5 || lk == KIND_XSPEC5;
+        pl->overlap = pl->fwd.size() == 2 && (pl->knobs.overlap > 0 || (pl->knobs.overlap < 0 && !gemm_last));
+    }
     if (pl->overlap) {
         if ((e = cudaStreamCreateWithFlags(&pl->aux_stream, cudaStreamNonBlocking)) != cudaSuccess ||
             (e = cudaEventCreateWithFlags(&pl->start_ev, cudaEventDisableTiming)) != cudaSuccess) {

@@ -104,6 +104,7 @@ def test_scaled_float_chunks_and_split_calls(monkeypatch):
     """Small chunk buffers (several chunks, both overlap slots of the per-channel
     scale array reused) and split calls equal one call and the oracle."""
     monkeypatch.setenv("OMNI_CHUNK_MB", "2")
+    monkeypatch.setenv("OMNI_OVERLAP", "1")
     levels = synth.hierarchy(*SHAPES["8x8 on 4x4"])
     dims = synth.lattice_dims(levels)
     x = synth.random_complex(dims, 5, 40, seed=504, dtype="cf32")
@@ -113,6 +114,9 @@ def test_scaled_float_chunks_and_split_calls(monkeypatch):
     split = vis(levels, x, "cf32", "mixed", calls=[13, 27])
     assert relerr_per_channel(one, ref).max() <= TOL_MIXED
     assert relerr_per_channel(split, ref).max() <= TOL_MIXED
+    monkeypatch.setenv("OMNI_OVERLAP", "0")
+    serial = vis(levels, x, "cf32", "mixed")
+    assert relerr_per_channel(serial, one).max() <= 1e-6
 
 
 def test_mixed_general_all_ones_exact_after_rounding():

@@ -394,10 +394,12 @@ def test_expired_tensor_core_wait_is_reported(monkeypatch):
     assert np.isfinite(V).all()
 
 
-@pytest.mark.parametrize("precision", ["fp32", "mixed"])
-def test_correlate_replays_from_a_cuda_graph(precision):
-    """omni_correlate (both streams of the overlapped passes) can be captured once
-    and replayed: two replays accumulate twice one call's |F|^2."""
+@pytest.mark.parametrize("precision, overlap", [("fp32", "1"), ("mixed", "1"), ("mixed", "0")])
+def test_correlate_replays_from_a_cuda_graph(precision, overlap, monkeypatch):
+    """omni_correlate (with and without the two streams of overlapped chunk
+    passes) can be captured once and replayed: two replays accumulate twice one
+    call's |F|^2."""
+    monkeypatch.setenv("OMNI_OVERLAP", overlap)
     w = synth.workload("hier2")
     x = synth.voltages(w, channels=2, samples=30).cuda()
     with omni.Plan(w.levels, 2, dtype="ci8", precision=precision) as plan:
