@@ -353,6 +353,17 @@ void choose_level(Pass& p) {
     p.W = p.inner == 1 ? 1 : 256 * lpt / p.L;
 }
 
+// Forward passes of 2048 and 4096 points: the three-step kernel (16-point register
+// transforms; the four-step split 64 x 32 or 64 x 64 held a 64-point column in
+// registers: 210-255 registers per thread, one or two CTAs per SM).  The inverse
+// passes keep the four-step kernel.
+void use_smem3(Pass& p) {
+    if (p.kind != KIND_SMEM || !smem3_supports(p.L) || 2 * p.n > p.L) return;
+    if (p.mode != MODE_MID && p.mode != MODE_LAST) return;
+    p.kind = KIND_SMEM3;
+    p.W = smem3_lines(p.L, p.mode, p.inner);
+}
+
 // FP64 values of one channel's accumulator: |F|^2 over the padded lattice, or
 // for a tile-hybrid plan the complex cross-spectra [n_tiles][n_tiles][L1 L2].
 int64_t acc_doubles(const omni_plan* pl) {
@@ -424,6 +435,7 @@ omni_status build_passes(omni_plan* pl) {
                 } else {
                     choose_kind(q);
                     if (q.n == q.L && q.L > 1 && q.kind == KIND_SMEM) q.kind = KIND_DIRECT;
+                    use_smem3(q);
                 }
                 level1.push_back(q);
             }
@@ -497,6 +509,7 @@ omni_status build_passes(omni_plan* pl) {
             // unpadded (beam) axes: full-length register FFTs up to 64 points,
             // direct DFTs otherwise (the shared-memory kernels assume padding)
             if (p.n == p.L && p.L > 1 && p.kind == KIND_SMEM) p.kind = KIND_DIRECT;
+            use_smem3(p);
         }
         if (p.mode == MODE_MID) pl->fwd_elems = std::max(pl->fwd_elems, p.outer * p.q_out * p.inner);
         pl->fwd.push_back(p);
@@ -588,7 +601,8 @@ void choose_chunks(omni_plan* pl) {
         case KIND_LEVEL:
         case KIND_TC_B:
         case KIND_TC5_B:
-        case KIND_SMEM: ctas = (last.inner + last.W - 1) / last.W; break;
+        case KIND_SMEM:
+        case KIND_SMEM3: ctas = (last.inner + last.W - 1) / last.W; break;
         case KIND_REG: ctas = (last.inner + 255) / 256; break;
         case KIND_XSPEC: ctas = xspec_ctas_per_channel(last); break;
         case KIND_XSPEC5:
@@ -601,6 +615,7 @@ void choose_chunks(omni_plan* pl) {
     const int first_src = pl->fwd.size() == 1 ? (pl->dtype == OMNI_IN_CI8 ? SRC_CI8 : SRC_CF32) : SRC_BUF;
     if (last.kind == KIND_LEVEL && level_last_occupancy(last, first_src, &per_sm) != cudaSuccess) per_sm = 0;
     if (last.kind == KIND_SMEM && smem_last_occupancy(last, first_src, &per_sm) != cudaSuccess) per_sm = 0;
+    if (last.kind == KIND_SMEM3 && smem3_last_occupancy(last, first_src, &per_sm) != cudaSuccess) per_sm = 0;
     if (last.kind == KIND_TC_B && tc_occupancy(KIND_TC_B, &per_sm) != cudaSuccess) per_sm = 0;
     if (last.kind == KIND_TC5_B && tc5_occupancy(&per_sm) != cudaSuccess) per_sm = 0;
     if (last.kind == KIND_XSPEC && xspec_occupancy(&per_sm) != cudaSuccess) per_sm = 0;
@@ -696,7 +711,7 @@ void release(omni_plan* pl) {
 }
 
 const char* kind_name(int k) {
-    return k == KIND_REG ? "reg" : k == KIND_SMEM ? "smem" : k == KIND_LEVEL ? "level"
+    return k == KIND_REG ? "reg" : k == KIND_SMEM ? "smem" : k == KIND_SMEM3 ? "smem3x" : k == KIND_LEVEL ? "level"
          : k == KIND_TC_A || k == KIND_TC_B ? "tc" : k == KIND_TC5_B ? "tcgen05-"
          : k == KIND_XSPEC ? "xspec" : k == KIND_XSPEC5 ? "xspec-tcgen05-" : k == KIND_COV5 ? "lagsum-tcgen05-"
          : "direct";

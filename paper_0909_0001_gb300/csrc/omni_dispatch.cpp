@@ -27,6 +27,7 @@ cudaError_t upload_twiddles_reg_b();
 cudaError_t upload_twiddles_smem_a();
 cudaError_t upload_twiddles_smem_b();
 cudaError_t upload_twiddles_smem_c();
+cudaError_t upload_twiddles_smem3();
 cudaError_t upload_twiddles_level_a();
 cudaError_t upload_twiddles_level_b();
 
@@ -37,6 +38,7 @@ cudaError_t launch_pass(const Pass& p, const PassArgs& a, cudaStream_t st) {
             return p.L <= 512 ? launch_smem_a(p, a, st)
                  : p.L <= 2048 ? launch_smem_b(p, a, st) : launch_smem_c(p, a, st);
         case KIND_LEVEL: return p.L <= 16 ? launch_level_a(p, a, st) : launch_level_b(p, a, st);
+        case KIND_SMEM3: return launch_smem3(p, a, st);
         case KIND_TC_A:
         case KIND_TC_B: return launch_tc(p, a, st);
         case KIND_TC5_B: return launch_tc5(p, a, st);
@@ -73,8 +75,8 @@ cudaError_t init_device_tables() {
     for (int d : done)
         if (d == dev) return cudaSuccess;
     for (auto up : {upload_twiddles_reg_a, upload_twiddles_reg_b, upload_twiddles_smem_a,
-                    upload_twiddles_smem_b, upload_twiddles_smem_c, upload_twiddles_level_a,
-                    upload_twiddles_level_b})
+                    upload_twiddles_smem_b, upload_twiddles_smem_c, upload_twiddles_smem3,
+                    upload_twiddles_level_a, upload_twiddles_level_b})
         if ((e = up()) != cudaSuccess) return e;
     if ((e = upload_tc_tables()) != cudaSuccess) return e;
     if ((e = upload_tc5_tables()) != cudaSuccess) return e;

@@ -1,0 +1,288 @@
+// omni_fft_smem3.cu -- three-step shared-memory forward transforms of 2048 and
+// 4096 points.
+//
+// L = L1 x L2 x L3 with L1 = L2 = 16 and L3 = 8 or 16, so that no register
+// transform is longer than 16 points (a 64-point column held in registers took
+// 210-255 registers and left one or two CTAs per SM).  With j = j3 + L3 j2 + M j1
+// (M = L2 L3) and k = k1 + L1 (k2 + L2 k3):
+//   step 1: L1-point DFTs over j1 for each j' = j3 + L3 j2, times w_L^(j' k1)
+//   step 2: L2-point DFTs over j2 for each (k1, j3), times w_M^(j3 k2)
+//   step 3: L3-point DFTs over j3 for each (k1, k2)
+// (the factorisation of w_L^(j k) into the three DFTs and two twiddle stages).
+// A CTA transforms W lines held in shared memory as [j1][j2][j3] with a row pitch
+// L3 + 1 and a plane pitch = 8 (mod 16) float2, so that each step's half-warps
+// touch 16 different bank pairs; the twiddles w_L^m sit in shared memory.  Lines
+// are W consecutive inner indices (strided axes), or, for an axis that is
+// innermost in memory, W consecutive outer lines read and written contiguously.
+// MID writes the spectrum through shared memory in natural order; LAST keeps
+// |X|^2 of the chunk's samples in registers and folds them into the FP64
+// accumulator once.  The forward inputs j >= L/2 are zero (padding): step 1
+// never reads them.
+#include "omni_fft_common.cuh"
+
+namespace omni {
+namespace {
+
+constexpr int kS3Threads = 512;
+
+template <int L1, int L2, int L3>
+struct S3Geom {
+    static constexpr int L = L1 * L2 * L3, M = L2 * L3;
+    static constexpr int P2 = L3 + 1;
+    static constexpr int P1 = L2 * P2 + ((8 - (L2 * P2) % 16 + 16) % 16);
+    static constexpr int PLANE = L1 * P1;
+    static_assert(P1 % 16 == 8, "plane pitch");
+    static_assert(PLANE >= L + L / 16, "the natural-order output fits the plane");
+};
+
+__device__ __forceinline__ int out_at(int k) { return k + (k >> 4); }  // natural order, 1 pad per 16
+
+template <int L1, int L2, int L3, int W, bool ROWS, int MODE, int SRC>
+__global__ void __launch_bounds__(kS3Threads) pass_smem3(Pass p, PassArgs a) {
+    using G = S3Geom<L1, L2, L3>;
+    constexpr int L = G::L, M = G::M, P1 = G::P1, P2 = G::P2, PLANE = G::PLANE;
+    constexpr int LOG1 = ilog2(L1), LOG2 = ilog2(L2), LOG3 = ilog2(L3);
+    constexpr int T1 = (W * M + kS3Threads - 1) / kS3Threads;       // step-1 tasks per thread
+    constexpr int T2 = (W * L1 * L3 + kS3Threads - 1) / kS3Threads;  // step 2
+    constexpr int T3 = (W * L1 * L2 + kS3Threads - 1) / kS3Threads;  // step 3
+    extern __shared__ float2 sm[];
+    float2* tw = sm;          // [L]: w_L^m
+    float2* lines = sm + L;   // [W][PLANE]
+    const int tid = threadIdx.x;
+    for (int m = tid; m < L; m += kS3Threads) tw[m] = g_tw4096[m * (kTwiddleN / L)];
+
+    const int n = p.n;  // inputs per line (<= L / 2)
+    const int64_t inner = p.inner;
+    int64_t b = blockIdx.x, o0 = 0, i0 = 0, s_first = 0, n_samples = 1, cc = 0;
+    if constexpr (ROWS) {  // W consecutive outer lines (inner == 1), one sample
+        const int64_t tiles = (p.outer + W - 1) / W;
+        o0 = (b % tiles) * W;
+        s_first = b / tiles;
+    } else {
+        const int64_t tiles = (inner + W - 1) / W;
+        i0 = (b % tiles) * W;
+        b /= tiles;
+        if constexpr (MODE == MODE_LAST) {
+            cc = b;  // outer == 1
+            s_first = cc * a.tc;
+            n_samples = a.tc;
+        } else {
+            o0 = b % p.outer;
+            s_first = b / p.outer;
+        }
+    }
+    // the lines this CTA has (the last tile may be short)
+    auto line_ok = [&](int w) { return ROWS ? o0 + w < p.outer : i0 + w < inner; };
+
+    float acc[T3][L3];
+#pragma unroll
+    for (int u = 0; u < T3; ++u)
+#pragma unroll
+        for (int k = 0; k < L3; ++k) acc[u][k] = 0.f;
+
+    for (int64_t ts = 0; ts < n_samples; ++ts) {
+        const int64_t s = s_first + ts;
+        const int64_t base = src_base(a, s);
+        // load: contiguous runs along the line (ROWS) or W inner indices per input
+        for (int e = tid; e < W * n; e += kS3Threads) {
+            int w, j;
+            if constexpr (ROWS) {
+                w = e / n;
+                j = e - w * n;
+            } else {
+                j = e / W;
+                w = e - j * W;
+            }
+            float2 x = make_float2(0.f, 0.f);
+            if (line_ok(w))
+                x = ROWS ? ld_src<SRC>(a.src, base + (o0 + w) * (int64_t)n + j)
+                         : ld_src<SRC>(a.src, base + o0 * (int64_t)n * inner + (int64_t)j * inner + i0 + w);
+            lines[w * PLANE + (j / M) * P1 + ((j / L3) % L2) * P2 + (j % L3)] = x;
+        }
+        __syncthreads();
+        // step 1: j' = j3 + L3 j2 fastest across the threads
+#pragma unroll
+        for (int u = 0; u < T1; ++u) {
+            const int t = tid + u * kS3Threads;
+            if (t < W * M) {
+                const int w = t / M, jp = t - w * M, j2 = jp / L3, j3 = jp - j2 * L3;
+                float2* col = lines + w * PLANE + j2 * P2 + j3;
+                float2 v[L1];
+#pragma unroll
+                for (int j1 = 0; j1 < L1; ++j1) v[j1] = j1 < L1 / 2 ? col[j1 * P1] : make_float2(0.f, 0.f);
+                fft_dif<L1, true>(v);
+#pragma unroll
+                for (int k1 = 0; k1 < L1; ++k1) {
+                    float2 y = v[brev(k1, LOG1)];
+                    const int e = (jp * k1) & (L - 1);
+                    if (e) y = cmul(y, tw[e]);
+                    col[k1 * P1] = y;
+                }
+            }
+        }
+        __syncthreads();
+        // step 2: (k1, j3), j3 fastest
+#pragma unroll
+        for (int u = 0; u < T2; ++u) {
+            const int t = tid + u * kS3Threads;
+            if (t < W * L1 * L3) {
+                const int j3 = t % L3, k1 = (t / L3) % L1, w = t / (L3 * L1);
+                float2* row = lines + w * PLANE + k1 * P1 + j3;
+                float2 v[L2];
+#pragma unroll
+                for (int j2 = 0; j2 < L2; ++j2) v[j2] = row[j2 * P2];
+                fft_dif<L2, false>(v);
+#pragma unroll
+                for (int k2 = 0; k2 < L2; ++k2) {
+                    float2 y = v[brev(k2, LOG2)];
+                    const int e = (L1 * j3 * k2) & (L - 1);
+                    if (e) y = cmul(y, tw[e]);
+                    row[k2 * P2] = y;
+                }
+            }
+        }
+        __syncthreads();
+        // step 3: (k1, k2), k2 fastest; X[k1 + L1 k2 + L1 L2 k3]
+        float2 out[T3][L3];
+#pragma unroll
+        for (int u = 0; u < T3; ++u) {
+            const int t = tid + u * kS3Threads;
+            if (t < W * L1 * L2) {
+                const int k2 = t % L2, k1 = (t / L2) % L1, w = t / (L2 * L1);
+                const float2* r = lines + w * PLANE + k1 * P1 + k2 * P2;
+                float2 v[L3];
+#pragma unroll
+                for (int j3 = 0; j3 < L3; ++j3) v[j3] = r[j3];
+                fft_dif<L3, false>(v);
+#pragma unroll
+                for (int k3 = 0; k3 < L3; ++k3) {
+                    out[u][k3] = v[brev(k3, LOG3)];
+                    if constexpr (MODE == MODE_LAST) acc[u][k3] += cnorm(out[u][k3]);
+                }
+            }
+        }
+        if constexpr (MODE == MODE_MID) {
+            // the spectrum in natural order through shared memory, then contiguous stores
+            __syncthreads();
+#pragma unroll
+            for (int u = 0; u < T3; ++u) {
+                const int t = tid + u * kS3Threads;
+                if (t < W * L1 * L2) {
+                    const int k2 = t % L2, k1 = (t / L2) % L1, w = t / (L2 * L1);
+#pragma unroll
+                    for (int k3 = 0; k3 < L3; ++k3)
+                        lines[w * PLANE + out_at(k1 + L1 * k2 + L1 * L2 * k3)] = out[u][k3];
+                }
+            }
+            __syncthreads();
+            float2* d = a.dst + s * a.dst_stride;
+            for (int e = tid; e < W * L; e += kS3Threads) {
+                int w, k;
+                if constexpr (ROWS) {
+                    w = e / L;
+                    k = e - w * L;
+                } else {
+                    k = e / W;
+                    w = e - k * W;
+                }
+                if (!line_ok(w)) continue;
+                const float2 x = lines[w * PLANE + out_at(k)];
+                if constexpr (ROWS) d[(o0 + w) * (int64_t)L + k] = x;
+                else d[o0 * (int64_t)L * inner + (int64_t)k * inner + i0 + w] = x;
+            }
+        }
+        __syncthreads();
+    }
+    if constexpr (MODE == MODE_LAST) {
+        double* P = a.P + (a.c0 + cc) * a.P_stride;
+#pragma unroll
+        for (int u = 0; u < T3; ++u) {
+            const int t = tid + u * kS3Threads;
+            if (t < W * L1 * L2) {
+                const int k2 = t % L2, k1 = (t / L2) % L1, w = t / (L2 * L1);
+                if (!line_ok(w)) continue;
+#pragma unroll
+                for (int k3 = 0; k3 < L3; ++k3)
+                    P[(int64_t)(k1 + L1 * k2 + L1 * L2 * k3) * inner + i0 + w] += (double)acc[u][k3];
+            }
+        }
+    }
+}
+
+template <int L1, int L2, int L3, int W, bool ROWS>
+constexpr size_t s3_smem() {
+    return sizeof(float2) * ((size_t)L1 * L2 * L3 + (size_t)W * S3Geom<L1, L2, L3>::PLANE);
+}
+
+template <int L1, int L2, int L3, int W, bool ROWS, int MODE, int SRC>
+cudaError_t launch_s3(const Pass& p, const PassArgs& a, cudaStream_t st) {
+    int64_t blocks;
+    if (ROWS) blocks = a.S * ((p.outer + W - 1) / W);
+    else blocks = (MODE == MODE_LAST ? a.S : a.S * p.outer) * ((p.inner + W - 1) / W);
+    if (blocks <= 0) return cudaSuccess;
+    constexpr size_t smem = s3_smem<L1, L2, L3, W, ROWS>();
+    auto k = pass_smem3<L1, L2, L3, W, ROWS, MODE, SRC>;
+    cudaError_t e = smem_limit_once((const void*)k, smem);
+    if (e != cudaSuccess) return e;
+    k<<<(unsigned)blocks, kS3Threads, smem, st>>>(p, a);
+    return cudaGetLastError();
+}
+
+// one length: lines along a strided axis (W = WC) or along the innermost axis (W = WR)
+template <int L1, int L2, int L3, int WC, int WR>
+cudaError_t launch_s3_len(const Pass& p, const PassArgs& a, cudaStream_t st) {
+    if (p.mode != MODE_MID && p.mode != MODE_LAST) return cudaErrorInvalidValue;
+    if (p.n > L1 * L2 * L3 / 2) return cudaErrorInvalidValue;
+    const bool rows = p.mode == MODE_MID && p.inner == 1;
+    if (p.W != (rows ? WR : WC)) return cudaErrorInvalidValue;
+    if (p.mode == MODE_LAST)
+        return dispatch_src<MODE_LAST>(a.src_kind, [&](auto S) {
+            return launch_s3<L1, L2, L3, WC, false, MODE_LAST, decltype(S)::value>(p, a, st);
+        });
+    return dispatch_src<MODE_MID>(a.src_kind, [&](auto S) {
+        return rows ? launch_s3<L1, L2, L3, WR, true, MODE_MID, decltype(S)::value>(p, a, st)
+                    : launch_s3<L1, L2, L3, WC, false, MODE_MID, decltype(S)::value>(p, a, st);
+    });
+}
+
+template <int L1, int L2, int L3, int WC>
+cudaError_t s3_last_occupancy_len(const Pass& p, int src_kind, int* blocks_per_sm) {
+    constexpr size_t smem = s3_smem<L1, L2, L3, WC, false>();
+    return dispatch_src<MODE_LAST>(src_kind, [&](auto S) {
+        auto k = pass_smem3<L1, L2, L3, WC, false, MODE_LAST, decltype(S)::value>;
+        cudaError_t e = smem_limit_once((const void*)k, smem);
+        if (e != cudaSuccess) return e;
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, kS3Threads, smem);
+    });
+}
+
+}  // namespace
+
+// this unit's copies of the twiddle tables (static per translation unit)
+cudaError_t upload_twiddles_smem3() { return upload_twiddles(); }
+
+bool smem3_supports(int L) { return L == 2048 || L == 4096; }
+
+int smem3_lines(int L, int mode, int64_t inner) {
+    const bool rows = mode == MODE_MID && inner == 1;
+    if (L == 2048) return rows ? 4 : 8;
+    return rows ? 2 : 4;
+}
+
+cudaError_t launch_smem3(const Pass& p, const PassArgs& a, cudaStream_t st) {
+    switch (p.L) {
+        case 2048: return launch_s3_len<16, 16, 8, 8, 4>(p, a, st);
+        case 4096: return launch_s3_len<16, 16, 16, 4, 2>(p, a, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t smem3_last_occupancy(const Pass& p, int src_kind, int* blocks_per_sm) {
+    switch (p.L) {
+        case 2048: return s3_last_occupancy_len<16, 16, 8, 8>(p, src_kind, blocks_per_sm);
+        case 4096: return s3_last_occupancy_len<16, 16, 16, 4>(p, src_kind, blocks_per_sm);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace omni

@@ -37,8 +37,9 @@ enum PassKind : int {
     KIND_TC5_B = 6,  // the same on 5th-generation tensor cores (tcgen05, tensor memory)
     KIND_XSPEC = 7,  // tile hybrid: cross-spectra of every tile pair summed over samples (LAST)
     KIND_XSPEC5 = 8, // the same as a tcgen05 GEMM per tile frequency over the samples (mixed precision)
-    KIND_COV5 = 9    // 2-level mixed path: block cross-spectra per level-1 frequency (tcgen05 GEMM over
+    KIND_COV5 = 9,   // 2-level mixed path: block cross-spectra per level-1 frequency (tcgen05 GEMM over
                      // the samples) summed by level-2 grid offset (LAST; L1 x L2 = the level-2 shape)
+    KIND_SMEM3 = 10  // forward three-step 16 x 16 x (8 | 16) through shared memory (2048, 4096 points)
 };
 
 // One axis transform.  The data of one sample (or channel) is viewed as
@@ -121,6 +122,12 @@ cudaError_t launch_tc5(const Pass& p, const PassArgs& a, cudaStream_t stream);
 cudaError_t launch_xspec(const Pass& p, const PassArgs& a, cudaStream_t stream);
 cudaError_t xspec_occupancy(int* blocks_per_sm);
 int64_t xspec_ctas_per_channel(const Pass& p);
+// Forward three-step passes of 2048 and 4096 points: lines per CTA (W consecutive
+// inner indices, or for an innermost MID axis W consecutive outer lines).
+bool smem3_supports(int L);
+int smem3_lines(int L, int mode, int64_t inner);
+cudaError_t launch_smem3(const Pass& p, const PassArgs& a, cudaStream_t stream);
+cudaError_t smem3_last_occupancy(const Pass& p, int src_kind, int* blocks_per_sm);
 bool xspec5_supports(int64_t n_tiles, int64_t K);  // <= 64 tiles, K a multiple of 4
 cudaError_t launch_xspec5(const Pass& p, const PassArgs& a, cudaStream_t stream);
 cudaError_t xspec5_occupancy(int* blocks_per_sm);

@@ -212,6 +212,16 @@ def test_degenerate_and_odd_shapes(levels):
     check(levels, x)
 
 
+@pytest.mark.parametrize("n1, n2", [(2048, 2), (2, 2048), (1024, 3), (3, 1024)])
+def test_long_axes_three_step_passes(n1, n2):
+    """Axes of 2048 and 1024 antennas (padded to 4096 and 2048): the forward
+    three-step passes, with lines along the innermost axis (W whole rows per CTA)
+    and along a strided axis (W inner indices per CTA, fewer than W here)."""
+    levels = [synth.Level(n1, n2, (1.0, 0.2, 0.0, 1.0))]
+    x = synth.random_complex([n1, n2], 2, 3, seed=77)
+    check(levels, x)
+
+
 def test_zero_samples_is_a_no_op():
     levels = [synth.Level(4, 4)]
     with omni.Plan(levels, 1) as plan:
