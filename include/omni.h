@@ -126,7 +126,9 @@ omni_status omni_plan_create(const omni_level* levels, int n_levels, int64_t n_c
  * a square level in one kernel) or one pass per axis, or, for the mixed path,
  * the share of each chunk's last pass on tensor cores (all, 0.3, 0.6) with the
  * rest on the FP32 level kernel, and level 1 on tensor cores or as the FP32
- * FFT.  Each candidate runs one warm-up and two timed omni_correlate calls on a
+ * FFT; and for padded axes of 2048 or 4096 points the radix split of their forward
+ * passes, three steps 16 x 16 x (8 | 16) or four steps 64 x (32 | 64).  Each candidate
+ * runs one warm-up and two timed omni_correlate calls on a
  * private stream (their accumulators are discarded).  cache_path (or NULL): a text file of one JSON object per line,
  * keyed by level shapes, precision, dtype, C, T and device name; a hit skips
  * the search (*from_cache = 1), a search appends its winner.  Errors: as

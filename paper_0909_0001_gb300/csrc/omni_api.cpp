@@ -225,6 +225,9 @@ struct Knobs {
     int lag_sum = 1;              // mixed: level 2 as block cross-spectra over time summed by grid
                                   // offset on tcgen05 (1), or per-sample level-2 DFT-GEMMs (0)
                                   // (OMNI_MIXED_LAGSUM)
+    int fft3 = 1;                 // forward 2048/4096-point axes as three steps 16 x 16 x (8|16) (1)
+                                  // or four steps 64 x (32|64) (0) (OMNI_FFT3; grid1024 FP32:
+                                  // 36.8 vs 60.3 ms per step)
 };
 
 Knobs knobs_from_env() {
@@ -236,6 +239,7 @@ Knobs knobs_from_env() {
     if (const char* e = std::getenv("OMNI_SPLIT_TC")) k.split_tc = std::atof(e);
     if (const char* e = std::getenv("OMNI_TC_STAGE_A")) k.tc_stage_a = std::atoi(e) != 0;
     if (const char* e = std::getenv("OMNI_MIXED_LAGSUM")) k.lag_sum = std::atoi(e) != 0;
+    if (const char* e = std::getenv("OMNI_FFT3")) k.fft3 = std::atoi(e) != 0;
     return k;
 }
 
@@ -357,8 +361,8 @@ void choose_level(Pass& p) {
 // transforms; the four-step split 64 x 32 or 64 x 64 held a 64-point column in
 // registers: 210-255 registers per thread, one or two CTAs per SM).  The inverse
 // passes keep the four-step kernel.
-void use_smem3(Pass& p) {
-    if (p.kind != KIND_SMEM || !smem3_supports(p.L) || 2 * p.n > p.L) return;
+void use_smem3(Pass& p, const Knobs& k) {
+    if (!k.fft3 || p.kind != KIND_SMEM || !smem3_supports(p.L) || 2 * p.n > p.L) return;
     if (p.mode != MODE_MID && p.mode != MODE_LAST) return;
     p.kind = KIND_SMEM3;
     p.W = smem3_lines(p.L, p.mode, p.inner);
@@ -435,7 +439,7 @@ omni_status build_passes(omni_plan* pl) {
                 } else {
                     choose_kind(q);
                     if (q.n == q.L && q.L > 1 && q.kind == KIND_SMEM) q.kind = KIND_DIRECT;
-                    use_smem3(q);
+                    use_smem3(q, pl->knobs);
                 }
                 level1.push_back(q);
             }
@@ -509,7 +513,7 @@ omni_status build_passes(omni_plan* pl) {
             // unpadded (beam) axes: full-length register FFTs up to 64 points,
             // direct DFTs otherwise (the shared-memory kernels assume padding)
             if (p.n == p.L && p.L > 1 && p.kind == KIND_SMEM) p.kind = KIND_DIRECT;
-            use_smem3(p);
+            use_smem3(p, pl->knobs);
         }
         if (p.mode == MODE_MID) pl->fwd_elems = std::max(pl->fwd_elems, p.outer * p.q_out * p.inner);
         pl->fwd.push_back(p);
@@ -1159,6 +1163,9 @@ bool tune_cache_read(const char* path, const std::string& key, Knobs& k) {
         t.level_passes = lp != 0;
         t.split_tc = sp;
         t.tc_stage_a = sa != 0;
+        int f3 = 1;
+        if (const char* r = std::strstr(line, "\"fft3\":")) std::sscanf(r, "\"fft3\": %d", &f3);
+        t.fft3 = f3 != 0;
         k = t;
         found = true;  // the last matching line wins
     }
@@ -1171,9 +1178,9 @@ void tune_cache_write(const char* path, const std::string& key, const Knobs& k, 
     FILE* f = std::fopen(path, "a");
     if (!f) return;
     std::fprintf(f, "{\"key\": \"%s\", \"chunk_mb\": %lld, \"chunk_channels\": %lld, \"overlap\": %d, "
-                    "\"level_passes\": %d, \"split_tc\": %.3f, \"tc_stage_a\": %d, \"ms\": %.4f}\n",
+                    "\"level_passes\": %d, \"split_tc\": %.3f, \"tc_stage_a\": %d, \"fft3\": %d, \"ms\": %.4f}\n",
                  key.c_str(), (long long)k.chunk_mb, (long long)k.chunk_channels, k.overlap, k.level_passes,
-                 k.split_tc, k.tc_stage_a, ms);
+                 k.split_tc, k.tc_stage_a, k.fft3, ms);
     std::fclose(f);
 }
 
@@ -1221,13 +1228,20 @@ omni_status omni_plan_create_tuned(const omni_level* levels, int n_levels, int64
                         cands.push_back(k);
                     }
             } else {
-                for (int lp : {1, 0}) {
-                    Knobs k;
-                    k.chunk_mb = mb;
-                    k.overlap = ov;
-                    k.level_passes = lp;
-                    cands.push_back(k);
-                }
+                // FP32: level passes or one pass per axis, and for 2048/4096-point axes
+                // the three- or four-step radix split
+                bool long_axes = false;
+                for (int d = 0; d < g.D; ++d) long_axes = long_axes || g.Lp[d] == 2048 || g.Lp[d] == 4096;
+                for (int lp : {1, 0})
+                    for (int f3 : {1, 0}) {
+                        if (!long_axes && f3 == 0) continue;
+                        Knobs k;
+                        k.chunk_mb = mb;
+                        k.overlap = ov;
+                        k.level_passes = lp;
+                        k.fft3 = f3;
+                        cands.push_back(k);
+                    }
             }
         }
     cudaStream_t stream = nullptr;

@@ -47,3 +47,24 @@ def test_tuned_mixed_plan():
     plan.close()
     assert knobs["chunk_mb"] in (384, 768, 1536, 3072)
     assert relerr_per_channel(V, oracle.correlate(w.dims, x)) <= 1e-4
+
+
+def test_tuner_searches_the_radix_split_of_long_axes(tmp_path):
+    """A 2048-point padded axis: the candidates include its three-step (16 x 16 x 8)
+    and four-step (64 x 32) forms; the winner's split is in the cache and its
+    visibilities match the oracle."""
+    levels = [synth.Level(1024, 2, (1.0, 0.3, 0.0, 1.0))]
+    dims = synth.lattice_dims(levels)
+    x = synth.random_complex(dims, 1, 4, seed=92)
+    xd = x.cuda()
+    cache = str(tmp_path / "tune.jsonl")
+    plan = omni.Plan.tuned(levels, 1, xd, dtype="cf32", cache=cache)
+    plan.correlate(xd)
+    V = plan.visibilities().cpu().numpy()
+    plan.close()
+    assert relerr_per_channel(V, oracle.correlate(dims, x)) <= 1e-5
+    entries = [json.loads(line) for line in open(cache)]
+    assert len(entries) == 1 and entries[0]["fft3"] in (0, 1)
+    again = omni.Plan.tuned(levels, 1, xd, dtype="cf32", cache=cache)
+    assert again.from_cache
+    again.close()
