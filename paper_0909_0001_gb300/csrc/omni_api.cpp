@@ -1690,12 +1690,15 @@ omni_status omni_correlate_host(omni_plan* pl, const void* volts_host, int64_t T
             OMNI_CUDA(cudaStreamWaitEvent(pl->split_stream, pl->start_ev, 0), "cudaStreamWaitEvent");
         for (int b = 0; b < 2; ++b) OMNI_CUDA(cudaEventRecord(pl->last_done[b], s), "cudaEventRecord");
     }
-    // equal-sized chunks (no short tail chunk paying a whole fold and launch)
+    // equal-sized chunks (no short tail chunk paying a whole fold and launch),
+    // except a first chunk of a quarter of the channels: nothing overlaps the
+    // first chunk's copy, so a smaller one starts the transforms sooner
     const int64_t Cb = ceil_div(pl->C, ceil_div(pl->C, pl->Cc));
     const int64_t Tb = ceil_div(T, ceil_div(T, pl->Tc));
+    const int64_t C_first = std::max<int64_t>(1, Cb / 4);
     int64_t j = 0;
-    for (int64_t c0 = 0; c0 < pl->C; c0 += Cb) {
-        const int64_t cc = std::min(Cb, pl->C - c0);
+    for (int64_t c0 = 0; c0 < pl->C;) {
+        const int64_t cc = std::min(c0 == 0 ? C_first : Cb, pl->C - c0);
         for (int64_t t0 = 0; t0 < T; t0 += Tb, ++j) {
             const int64_t tc = std::min(Tb, T - t0);
             const int b = (int)(j & 1);
@@ -1714,6 +1717,7 @@ omni_status omni_correlate_host(omni_plan* pl, const void* volts_host, int64_t T
             if (st != OMNI_OK) return st;
             OMNI_CUDA(cudaEventRecord(pl->freed[b], s), "cudaEventRecord");
         }
+        c0 += cc;
     }
     OMNI_CUDA(cudaStreamSynchronize(pl->copy_stream), "cudaStreamSynchronize(copy)");
     return OMNI_OK;
