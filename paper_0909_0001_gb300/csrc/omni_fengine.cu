@@ -262,6 +262,131 @@ __global__ void __launch_bounds__(kFThreads) fengine_fused(const int8_t* __restr
     }
 }
 
+// F = 64 (128-sample frames): eight lanes per (antenna, frame) transform, the
+// 64-point FFT as 8 x 8 in registers (m = l + 8 q on lane l, k = k_a + 8 k_b):
+//   step 1: lane l: 8-point DFT over q, times w_64^(l k_a)
+//   step 2: lane k_a: 8-point DFT over l (the 8 x 8 transpose through a per-warp
+//           shared buffer, warp-synchronous: no CTA barrier inside a transform)
+// then Z(64 - f) from the partner lane by shuffles, the real-spectrum unpacking and
+// calibration.  CTA = 32 consecutive antennas (a warp: 4 of them) x kF64Frames
+// frames; per frame the 64 x 32 spectrum is staged so that each (channel, frame)
+// row of 32 antennas is one 64-byte (int8) or 256-byte (FP32) store.  Buffer index
+// of point m: 9 (m / 8) + m % 8 and a transform pitch of 72: the half-warps of every
+// step touch 16 different bank pairs.
+constexpr int kF64Ant = 32;
+constexpr int kF64Frames = 8;
+constexpr int kF64MaxTaps = 8;
+
+template <bool I8>
+__global__ void __launch_bounds__(256) fengine64(const int8_t* __restrict__ raw, int64_t N, int64_t S, int P,
+                                                 const float* __restrict__ w, int64_t T,
+                                                 const float2* __restrict__ gains, float scale,
+                                                 void* __restrict__ out) {
+    __shared__ float2 zs[8][4 * 72];              // per warp: 4 transforms
+    __shared__ float2 ys[64][kF64Ant + 1];        // one frame's spectra, [channel][antenna]
+    __shared__ __align__(16) float wsm[kF64MaxTaps * 128];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tr = lane >> 3, l = lane & 7;
+    for (int i = tid; i < P * 128; i += 256) wsm[i] = w ? w[i] : 1.f;
+    const int64_t tchunks = (T + kF64Frames - 1) / kF64Frames;
+    const int64_t a0 = (blockIdx.x / tchunks) * kF64Ant, t0 = (blockIdx.x % tchunks) * kF64Frames;
+    const int al = 4 * warp + tr;  // antenna within the CTA
+    const int64_t a = a0 + al;
+    float2* buf = zs[warp] + 72 * tr;
+    // unpacking twiddles e^{-i pi f / 64} and the gains of this lane's f = l + 8 k_b
+    float2 ut[8], gl[8];
+#pragma unroll
+    for (int kb = 0; kb < 8; ++kb) {
+        ut[kb] = g_fetw[(l + 8 * kb) * 64];
+        gl[kb] = (gains && a < N) ? __ldg(gains + (int64_t)(l + 8 * kb) * N + a) : make_float2(1.f, 0.f);
+    }
+    __syncthreads();
+    for (int64_t t = t0; t < t0 + kF64Frames && t < T; ++t) {
+        // polyphase sums of samples 16 l .. 16 l + 15: z(8 l + q) = u(16 l + 2q) + i u(16 l + 2q + 1)
+        float ue[8], uo[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) ue[q] = uo[q] = 0.f;
+        if (a < N) {
+            const int8_t* ra = raw + a * S + 16 * l;
+            for (int p = 0; p < P; ++p) {
+                const int4 rv = __ldg(reinterpret_cast<const int4*>(ra + (t + p) * 128));
+                const int8_t* r = reinterpret_cast<const int8_t*>(&rv);
+                const float4* w4 = reinterpret_cast<const float4*>(wsm + p * 128 + 16 * l);
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    const float4 ww = w4[h];
+                    ue[2 * h] = fmaf(ww.x, (float)r[4 * h], ue[2 * h]);
+                    uo[2 * h] = fmaf(ww.y, (float)r[4 * h + 1], uo[2 * h]);
+                    ue[2 * h + 1] = fmaf(ww.z, (float)r[4 * h + 2], ue[2 * h + 1]);
+                    uo[2 * h + 1] = fmaf(ww.w, (float)r[4 * h + 3], uo[2 * h + 1]);
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) buf[9 * l + q] = make_float2(ue[q], uo[q]);  // point m = 8 l + q
+        __syncwarp();
+        // step 1: lane l holds z(l + 8 q), q < 8 (buffer index 9 q + l)
+        float2 v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[q] = buf[9 * q + l];
+        fft_dif<8, false>(v);
+        __syncwarp();
+#pragma unroll
+        for (int ka = 0; ka < 8; ++ka) {
+            float2 y = v[brev(ka, 3)];
+            if (l * ka) y = cmul(y, c_tw64[(l * ka) & 63]);
+            buf[9 * ka + l] = y;  // Y[l][k_a]
+        }
+        __syncwarp();
+        // step 2: lane k_a = l holds Y[0..7][k_a] -> Z(k_a + 8 k_b) = v[brev(k_b)]
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = buf[9 * l + j];
+        fft_dif<8, false>(v);
+        __syncwarp();
+        // Z(64 - f) for f = k_a + 8 k_b lives on lane (8 - k_a) mod 8 of this transform
+        float2 zp[8];
+        const int src = (lane & ~7) | ((8 - l) & 7);
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const float2 mine = v[brev(r, 3)];
+            zp[r] = make_float2(__shfl_sync(0xffffffffu, mine.x, src), __shfl_sync(0xffffffffu, mine.y, src));
+        }
+#pragma unroll
+        for (int kb = 0; kb < 8; ++kb) {
+            const int f = l + 8 * kb;
+            const float2 zf = v[brev(kb, 3)];
+            // 64 - f = (8 - l) + 8 (7 - k_b) for l > 0, 8 (8 - k_b) for l = 0
+            const float2 zc = l ? zp[(7 - kb) & 7] : zp[(8 - kb) & 7];
+            const float2 e = make_float2(0.5f * (zf.x + zc.x), 0.5f * (zf.y - zc.y));
+            const float2 o = make_float2(0.5f * (zf.y + zc.y), -0.5f * (zf.x - zc.x));
+            const float2 x = cadd(e, cmul(o, ut[kb]));
+            ys[f][al] = calibrate(x, gl[kb], scale);
+        }
+        __syncthreads();
+        // rows (channel f, frame t) of the CTA's 32 antennas
+        if (I8) {
+            const int f = tid >> 2, q = tid & 3;  // 8 antennas (16 bytes) per thread
+            if (a0 + 8 * q < N) {
+                char2 c[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) c[k] = make_char2(quantize8(ys[f][8 * q + k].x), quantize8(ys[f][8 * q + k].y));
+                char2* o = reinterpret_cast<char2*>(out) + ((int64_t)f * T + t) * N + a0 + 8 * q;
+                if (a0 + 8 * q + 8 <= N && ((uintptr_t)o % 16) == 0) {
+                    *reinterpret_cast<int4*>(o) = *reinterpret_cast<const int4*>(c);
+                } else {
+                    for (int k = 0; k < 8 && a0 + 8 * q + k < N; ++k) o[k] = c[k];
+                }
+            }
+        } else {
+            for (int e = tid; e < 64 * kF64Ant; e += 256) {
+                const int f = e / kF64Ant, k = e - f * kF64Ant;
+                if (a0 + k < N) reinterpret_cast<float2*>(out)[((int64_t)f * T + t) * N + a0 + k] = ys[f][k];
+            }
+        }
+        __syncthreads();
+    }
+}
+
 cudaError_t upload_fengine_twiddles() {
     static float2 h[4096];
     for (int j = 0; j < 4096; ++j) {
@@ -310,11 +435,18 @@ cudaError_t launch_fengine(const int8_t* raw, int64_t N, int64_t S, int32_t F, i
             std::lock_guard<std::mutex> lock(mu);
             if (std::find(done.begin(), done.end(), dev) == done.end()) {
                 if ((e = upload_fengine_twiddles()) != cudaSuccess) return e;
+                if ((e = upload_twiddles()) != cudaSuccess) return e;  // this unit's FFT tables
                 done.push_back(dev);
             }
         }
-        const unsigned ctas = (unsigned)fengine_ctas(N, T, F);
         const bool vec = F >= 8 && S % 16 == 0 && (uintptr_t)raw % 16 == 0 && (uintptr_t)window % 16 == 0;
+        if (F == 64 && vec && P <= kF64MaxTaps) {
+            const unsigned c64 = (unsigned)(((N + kF64Ant - 1) / kF64Ant) * ((T + kF64Frames - 1) / kF64Frames));
+            if (out_i8) fengine64<true><<<c64, 256, 0, st>>>(raw, N, S, P, window, T, gains, scale, out);
+            else fengine64<false><<<c64, 256, 0, st>>>(raw, N, S, P, window, T, gains, scale, out);
+            return cudaGetLastError();
+        }
+        const unsigned ctas = (unsigned)fengine_ctas(N, T, F);
         if (out_i8 && vec)
             fengine_fused<true, true><<<ctas, kFThreads, 0, st>>>(raw, N, S, F, logF, P, window, T, gains, scale, out);
         else if (out_i8)

@@ -28,7 +28,10 @@ def run(raw, F, P=1, window=None, gains=None, scale=1.0, dtype="cf32"):
 
 
 @pytest.mark.parametrize("N, F, P, extra", [(3, 8, 1, 0), (5, 64, 4, 17), (33, 256, 8, 3), (2, 2, 1, 1),
-                                            (7, 4096, 2, 0), (40, 32, 3, 31)])
+                                            (7, 4096, 2, 0), (40, 32, 3, 31),
+                                            # F = 64 with 16-byte rows: the radix-8 x 8 kernel, a
+                                            # partial 32-antenna group, one tap and eight
+                                            (40, 64, 4, 0), (33, 64, 1, 16), (70, 64, 8, 32)])
 def test_fengine_matches_oracle(N, F, P, extra):
     rng = np.random.default_rng(N * 1000 + F)
     T = 6
@@ -43,7 +46,7 @@ def test_fengine_matches_oracle(N, F, P, extra):
     assert relerr(Y, ref) <= TOL
 
 
-@pytest.mark.parametrize("F", [128, 512])      # the fused pass and the two-kernel pass
+@pytest.mark.parametrize("F", [64, 128, 512])  # the radix-8 x 8 pass, the fused pass, the two-kernel pass
 def test_fengine_int8_codes_are_the_quantised_floats(F):
     rng = np.random.default_rng(7)
     N, P, T = 9, 4, 10
