@@ -277,8 +277,9 @@ constexpr int kF64Ant = 32;
 constexpr int kF64Frames = 8;
 constexpr int kF64MaxTaps = 8;
 
+// (three CTAs per SM: 6.33 against 6.82 ms on the 64-channel bench leg at two)
 template <bool I8>
-__global__ void __launch_bounds__(256) fengine64(const int8_t* __restrict__ raw, int64_t N, int64_t S, int P,
+__global__ void __launch_bounds__(256, 3) fengine64(const int8_t* __restrict__ raw, int64_t N, int64_t S, int P,
                                                  const float* __restrict__ w, int64_t T,
                                                  const float2* __restrict__ gains, float scale,
                                                  void* __restrict__ out) {
