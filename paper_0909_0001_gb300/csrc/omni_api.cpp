@@ -1690,15 +1690,17 @@ omni_status omni_correlate_host(omni_plan* pl, const void* volts_host, int64_t T
             OMNI_CUDA(cudaStreamWaitEvent(pl->split_stream, pl->start_ev, 0), "cudaStreamWaitEvent");
         for (int b = 0; b < 2; ++b) OMNI_CUDA(cudaEventRecord(pl->last_done[b], s), "cudaEventRecord");
     }
-    // equal-sized chunks (no short tail chunk paying a whole fold and launch),
-    // except a first chunk of a quarter of the channels: nothing overlaps the
-    // first chunk's copy, so a smaller one starts the transforms sooner
+    // chunks growing from a quarter of the plan's chunk: nothing overlaps the
+    // first chunk's copy, and each next copy (host copies ran at 210 GB/s, about
+    // three quarters of the transforms' rate on the 2-level workload) must fit in
+    // the previous chunk's transforms, so the channel count grows by 30% a chunk
     const int64_t Cb = ceil_div(pl->C, ceil_div(pl->C, pl->Cc));
     const int64_t Tb = ceil_div(T, ceil_div(T, pl->Tc));
-    const int64_t C_first = std::max<int64_t>(1, Cb / 4);
+    int64_t next = std::max<int64_t>(1, Cb / 4);
     int64_t j = 0;
     for (int64_t c0 = 0; c0 < pl->C;) {
-        const int64_t cc = std::min(c0 == 0 ? C_first : Cb, pl->C - c0);
+        const int64_t cc = std::min(next, pl->C - c0);
+        next = std::min<int64_t>(Cb, std::max<int64_t>(next + 1, (next * 13 + 9) / 10));
         for (int64_t t0 = 0; t0 < T; t0 += Tb, ++j) {
             const int64_t tc = std::min(Tb, T - t0);
             const int b = (int)(j & 1);
