@@ -10,8 +10,9 @@
 //   step 3: L3-point DFTs over j3 for each (k1, k2)
 // (the factorisation of w_L^(j k) into the three DFTs and two twiddle stages).
 // A CTA transforms W lines held in shared memory as [j1][j2][j3] with a row pitch
-// L3 + 1 and a plane pitch = 8 (mod 16) float2, so that each step's half-warps
-// touch 16 different bank pairs; the twiddles w_L^m sit in shared memory.  Lines
+// L3 + 1, a j1 pitch = 8 and a line pitch = 2 (mod 16) float2, so that each step's
+// half-warps touch 16 different bank pairs; each thread reads one twiddle w^j from
+// a shared-memory table and forms the powers it needs in registers.  Lines
 // are W consecutive inner indices (strided axes), or, for an axis that is
 // innermost in memory, W consecutive outer lines read and written contiguously.
 // MID writes the spectrum through shared memory in natural order; LAST keeps
@@ -30,12 +31,33 @@ struct S3Geom {
     static constexpr int L = L1 * L2 * L3, M = L2 * L3;
     static constexpr int P2 = L3 + 1;
     static constexpr int P1 = L2 * P2 + ((8 - (L2 * P2) % 16 + 16) % 16);
-    static constexpr int PLANE = L1 * P1;
-    static_assert(P1 % 16 == 8, "plane pitch");
+    // lines 2 float2 apart mod 16: the W lines of a strided load land in different banks
+    static constexpr int PLANE = L1 * P1 + ((2 - (L1 * P1) % 16 + 16) % 16);
+    static_assert(P1 % 16 == 8 && PLANE % 16 == 2, "pitches");
     static_assert(PLANE >= L + L / 16, "the natural-order output fits the plane");
 };
 
 __device__ __forceinline__ int out_at(int k) { return k + (k >> 4); }  // natural order, 1 pad per 16
+
+// w^k for k < 16 from w^1 (one shared-memory read per thread instead of a read of
+// w^(j k) per k, whose stride k across the lanes conflicted): powers 1..3 and
+// 4, 8, 12 by squaring, then w^(4a + b) = w^(4a) w^b (at most six roundings)
+struct Pow16 {
+    float2 p[4], q[4];  // w^b, w^(4a)
+    __device__ __forceinline__ explicit Pow16(float2 w) {
+        p[0] = make_float2(1.f, 0.f);
+        p[1] = w;
+        p[2] = cmul(w, w);
+        p[3] = cmul(p[2], w);
+        q[0] = p[0];
+        q[1] = cmul(p[2], p[2]);
+        q[2] = cmul(q[1], q[1]);
+        q[3] = cmul(q[2], q[1]);
+    }
+    __device__ __forceinline__ float2 operator()(int k) const {  // k a compile-time constant after unrolling
+        return (k & 3) == 0 ? q[k >> 2] : (k < 4 ? p[k] : cmul(q[k >> 2], p[k & 3]));
+    }
+};
 
 template <int L1, int L2, int L3, int W, bool ROWS, int MODE, int SRC>
 __global__ void __launch_bounds__(kS3Threads) pass_smem3(Pass p, PassArgs a) {
@@ -111,11 +133,11 @@ __global__ void __launch_bounds__(kS3Threads) pass_smem3(Pass p, PassArgs a) {
 #pragma unroll
                 for (int j1 = 0; j1 < L1; ++j1) v[j1] = j1 < L1 / 2 ? col[j1 * P1] : make_float2(0.f, 0.f);
                 fft_dif<L1, true>(v);
+                const Pow16 pw(tw[jp]);  // w_L^(j' k1)
 #pragma unroll
                 for (int k1 = 0; k1 < L1; ++k1) {
                     float2 y = v[brev(k1, LOG1)];
-                    const int e = (jp * k1) & (L - 1);
-                    if (e) y = cmul(y, tw[e]);
+                    if (k1) y = cmul(y, pw(k1));
                     col[k1 * P1] = y;
                 }
             }
@@ -132,11 +154,11 @@ __global__ void __launch_bounds__(kS3Threads) pass_smem3(Pass p, PassArgs a) {
 #pragma unroll
                 for (int j2 = 0; j2 < L2; ++j2) v[j2] = row[j2 * P2];
                 fft_dif<L2, false>(v);
+                const Pow16 pw(tw[L1 * j3]);  // w_M^(j3 k2) = w_L^(L1 j3 k2)
 #pragma unroll
                 for (int k2 = 0; k2 < L2; ++k2) {
                     float2 y = v[brev(k2, LOG2)];
-                    const int e = (L1 * j3 * k2) & (L - 1);
-                    if (e) y = cmul(y, tw[e]);
+                    if (k2) y = cmul(y, pw(k2));
                     row[k2 * P2] = y;
                 }
             }
