@@ -225,9 +225,9 @@ struct Knobs {
     int lag_sum = 1;              // mixed: level 2 as block cross-spectra over time summed by grid
                                   // offset on tcgen05 (1), or per-sample level-2 DFT-GEMMs (0)
                                   // (OMNI_MIXED_LAGSUM)
-    int fft3 = 1;                 // forward 2048/4096-point axes as three steps 16 x 16 x (8|16) (1)
+    int fft3 = 1;                 // 2048/4096-point axes as three steps 16 x 16 x (8|16) (1)
                                   // or four steps 64 x (32|64) (0) (OMNI_FFT3; grid1024 FP32:
-                                  // 36.8 vs 60.3 ms per step)
+                                  // 23.6 vs 60.3 ms per step)
 };
 
 Knobs knobs_from_env() {
@@ -357,13 +357,13 @@ void choose_level(Pass& p) {
     p.W = p.inner == 1 ? 1 : 256 * lpt / p.L;
 }
 
-// Forward passes of 2048 and 4096 points: the three-step kernel (16-point register
+// Passes of 2048 and 4096 points: the three-step kernel (16-point register
 // transforms; the four-step split 64 x 32 or 64 x 64 held a 64-point column in
-// registers: 210-255 registers per thread, one or two CTAs per SM).  The inverse
-// passes keep the four-step kernel.
+// registers: 210-255 registers per thread, one or two CTAs per SM).
 void use_smem3(Pass& p, const Knobs& k) {
-    if (!k.fft3 || p.kind != KIND_SMEM || !smem3_supports(p.L) || 2 * p.n > p.L) return;
-    if (p.mode != MODE_MID && p.mode != MODE_LAST) return;
+    if (!k.fft3 || p.kind != KIND_SMEM || !smem3_supports(p.L)) return;
+    const bool fwd = p.mode == MODE_MID || p.mode == MODE_LAST;
+    if (fwd && 2 * p.n > p.L) return;
     p.kind = KIND_SMEM3;
     p.W = smem3_lines(p.L, p.mode, p.inner);
 }
@@ -564,6 +564,7 @@ omni_status build_passes(omni_plan* pl) {
         if (pl->n_tiles) p.outer *= pl->n_tiles * pl->n_tiles;
         p.mode = (a == 0) ? MODE_INV_LAST : MODE_INV_MID;
         choose_kind(p);
+        use_smem3(p, pl->knobs);
         if (p.mode == MODE_INV_MID) pl->inv_elems = std::max(pl->inv_elems, p.outer * p.q_out * p.inner);
         pl->inv.push_back(p);
     }

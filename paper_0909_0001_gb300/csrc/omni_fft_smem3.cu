@@ -9,13 +9,15 @@
 //   step 2: L2-point DFTs over j2 for each (k1, j3), times w_M^(j3 k2)
 //   step 3: L3-point DFTs over j3 for each (k1, k2)
 // (the factorisation of w_L^(j k) into the three DFTs and two twiddle stages).
+// The inverse passes use the same transform (the inverse runs as a forward FFT)
+// on all L inputs and keep the lag slots, the last one conjugated and scaled.
 // A CTA transforms W lines held in shared memory as [j1][j2][j3] with a row pitch
 // L3 + 1, a j1 pitch = 8 and a line pitch = 2 (mod 16) float2, so that each step's
 // half-warps touch 16 different bank pairs; each thread reads one twiddle w^j from
 // a shared-memory table and forms the powers it needs in registers.  Lines
 // are W consecutive inner indices (strided axes), or, for an axis that is
 // innermost in memory, W consecutive outer lines read and written contiguously.
-// MID writes the spectrum through shared memory in natural order; LAST keeps
+// MID and the inverse passes write through shared memory in natural order; LAST keeps
 // |X|^2 of the chunk's samples in registers and folds them into the FP64
 // accumulator once.  The forward inputs j >= L/2 are zero (padding): step 1
 // never reads them.
@@ -63,6 +65,7 @@ template <int L1, int L2, int L3, int W, bool ROWS, int MODE, int SRC>
 __global__ void __launch_bounds__(kS3Threads) pass_smem3(Pass p, PassArgs a) {
     using G = S3Geom<L1, L2, L3>;
     constexpr int L = G::L, M = G::M, P1 = G::P1, P2 = G::P2, PLANE = G::PLANE;
+    constexpr bool FWD = MODE == MODE_MID || MODE == MODE_LAST;  // forward: inputs j >= L/2 are zero
     constexpr int LOG1 = ilog2(L1), LOG2 = ilog2(L2), LOG3 = ilog2(L3);
     constexpr int T1 = (W * M + kS3Threads - 1) / kS3Threads;       // step-1 tasks per thread
     constexpr int T2 = (W * L1 * L3 + kS3Threads - 1) / kS3Threads;  // step 2
@@ -131,8 +134,9 @@ __global__ void __launch_bounds__(kS3Threads) pass_smem3(Pass p, PassArgs a) {
                 float2* col = lines + w * PLANE + j2 * P2 + j3;
                 float2 v[L1];
 #pragma unroll
-                for (int j1 = 0; j1 < L1; ++j1) v[j1] = j1 < L1 / 2 ? col[j1 * P1] : make_float2(0.f, 0.f);
-                fft_dif<L1, true>(v);
+                for (int j1 = 0; j1 < L1; ++j1)
+                    v[j1] = (!FWD || j1 < L1 / 2) ? col[j1 * P1] : make_float2(0.f, 0.f);
+                fft_dif<L1, FWD>(v);
                 const Pow16 pw(tw[jp]);  // w_L^(j' k1)
 #pragma unroll
                 for (int k1 = 0; k1 < L1; ++k1) {
@@ -183,7 +187,7 @@ __global__ void __launch_bounds__(kS3Threads) pass_smem3(Pass p, PassArgs a) {
                 }
             }
         }
-        if constexpr (MODE == MODE_MID) {
+        if constexpr (MODE != MODE_LAST) {
             // the spectrum in natural order through shared memory, then contiguous stores
             __syncthreads();
 #pragma unroll
@@ -197,6 +201,29 @@ __global__ void __launch_bounds__(kS3Threads) pass_smem3(Pass p, PassArgs a) {
                 }
             }
             __syncthreads();
+            if constexpr (!FWD) {
+                // inverse: the kept lags, slot q = bin (q - q_shift) mod L; the last
+                // pass conjugates and scales (the inverse runs as a forward FFT)
+                const int Q = p.q_out;
+                for (int e = tid; e < W * Q; e += kS3Threads) {
+                    int w, q;
+                    if constexpr (ROWS) {
+                        w = e / Q;
+                        q = e - w * Q;
+                    } else {
+                        q = e / W;
+                        w = e - q * W;
+                    }
+                    if (!line_ok(w)) continue;
+                    const float2 x = lines[w * PLANE + out_at(inv_bin(q, p.q_shift, L))];
+                    const int64_t o = ROWS ? o0 + w : o0, i = ROWS ? 0 : i0 + w;
+                    const int64_t at = (o * Q + q) * inner + i;
+                    if constexpr (MODE == MODE_INV_MID)
+                        a.dst[s * a.dst_stride + at] = x;
+                    else
+                        a.V[(a.c0 + s) * a.V_stride + at] = make_double2((double)x.x * a.scale, -(double)x.y * a.scale);
+                }
+            } else {
             float2* d = a.dst + s * a.dst_stride;
             for (int e = tid; e < W * L; e += kS3Threads) {
                 int w, k;
@@ -211,6 +238,7 @@ __global__ void __launch_bounds__(kS3Threads) pass_smem3(Pass p, PassArgs a) {
                 const float2 x = lines[w * PLANE + out_at(k)];
                 if constexpr (ROWS) d[(o0 + w) * (int64_t)L + k] = x;
                 else d[o0 * (int64_t)L * inner + (int64_t)k * inner + i0 + w] = x;
+            }
             }
         }
         __syncthreads();
@@ -253,17 +281,24 @@ cudaError_t launch_s3(const Pass& p, const PassArgs& a, cudaStream_t st) {
 // one length: lines along a strided axis (W = WC) or along the innermost axis (W = WR)
 template <int L1, int L2, int L3, int WC, int WR>
 cudaError_t launch_s3_len(const Pass& p, const PassArgs& a, cudaStream_t st) {
-    if (p.mode != MODE_MID && p.mode != MODE_LAST) return cudaErrorInvalidValue;
-    if (p.n > L1 * L2 * L3 / 2) return cudaErrorInvalidValue;
-    const bool rows = p.mode == MODE_MID && p.inner == 1;
+    const bool fwd = p.mode == MODE_MID || p.mode == MODE_LAST;
+    if (p.n > (fwd ? L1 * L2 * L3 / 2 : L1 * L2 * L3)) return cudaErrorInvalidValue;
+    const bool rows = p.mode != MODE_LAST && p.inner == 1;
     if (p.W != (rows ? WR : WC)) return cudaErrorInvalidValue;
     if (p.mode == MODE_LAST)
         return dispatch_src<MODE_LAST>(a.src_kind, [&](auto S) {
             return launch_s3<L1, L2, L3, WC, false, MODE_LAST, decltype(S)::value>(p, a, st);
         });
-    return dispatch_src<MODE_MID>(a.src_kind, [&](auto S) {
-        return rows ? launch_s3<L1, L2, L3, WR, true, MODE_MID, decltype(S)::value>(p, a, st)
-                    : launch_s3<L1, L2, L3, WC, false, MODE_MID, decltype(S)::value>(p, a, st);
+    return dispatch_mode(p.mode, [&](auto Mc) {
+        constexpr int MO = decltype(Mc)::value;
+        if constexpr (MO == MODE_LAST) {
+            return cudaErrorInvalidValue;
+        } else {
+            return dispatch_src<MO>(a.src_kind, [&](auto S) {
+                return rows ? launch_s3<L1, L2, L3, WR, true, MO, decltype(S)::value>(p, a, st)
+                            : launch_s3<L1, L2, L3, WC, false, MO, decltype(S)::value>(p, a, st);
+            });
+        }
     });
 }
 
@@ -286,7 +321,7 @@ cudaError_t upload_twiddles_smem3() { return upload_twiddles(); }
 bool smem3_supports(int L) { return L == 2048 || L == 4096; }
 
 int smem3_lines(int L, int mode, int64_t inner) {
-    const bool rows = mode == MODE_MID && inner == 1;
+    const bool rows = mode != MODE_LAST && inner == 1;
     if (L == 2048) return rows ? 4 : 8;
     return rows ? 2 : 4;
 }
