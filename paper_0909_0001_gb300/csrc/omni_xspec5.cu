@@ -87,6 +87,7 @@ constexpr int kXScaleTarget = 12;  // FP16: |Y| 2^-e <= 2^12
 constexpr uint32_t kIdesc128 = (1u << 4) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
 constexpr uint32_t kIdesc128Bf16 = kIdesc128 | (1u << 7) | (1u << 10);
 constexpr long long kWaitCycles = 4000000000LL;   // ~2 s
+constexpr long long kTestWaitCycles = 1000000LL;  // the forced-expiry test hook: ~0.5 ms
 
 __host__ __device__ inline int tile_off(int row, int k) {
     return (row >> 3) * kSBO + (k >> 3) * kLBO + (row & 7) * 16 + (k & 7) * 2;
@@ -222,6 +223,7 @@ __global__ void __launch_bounds__(kXThreads, 1) xspec5(Pass p, PassArgs a, const
     // operand stages, 1024-byte aligned
     unsigned char* dsm = reinterpret_cast<unsigned char*>(((uintptr_t)dsm_raw + 1023) & ~(uintptr_t)1023);
     __shared__ __align__(8) uint64_t full[kXStagesMax], empty[kXStagesMax], done, raw_full[kXRaw], raw_empty[kXRaw];
+    __shared__ __align__(8) uint64_t never_bar;  // test hook: nothing arrives on it
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
 
@@ -234,6 +236,10 @@ __global__ void __launch_bounds__(kXThreads, 1) xspec5(Pass p, PassArgs a, const
     const int tc = a.tc;
     const int steps = (tc + 15) / 16;
     const int e_scale = scale_exp(p, a, cc);
+    // pipeline waits (the test hook shortens them and makes the converters' first
+    // one wait for a phase that never comes); the drains keep the full budget, so
+    // that no copy or MMA is in flight when the CTA frees its memory
+    const long long budget = a.force_expire ? kTestWaitCycles : kWaitCycles;
     const double fold = ldexp(1.0, 2 * e_scale) * (p.unscaled_in || p.bf16 ? 1.0 : 256.0);
 
     if (warp == 0) {
@@ -247,6 +253,7 @@ __global__ void __launch_bounds__(kXThreads, 1) xspec5(Pass p, PassArgs a, const
             mbar_init(&empty[i], 1);
         }
         mbar_init(&done, 1);
+        mbar_init(&never_bar, 1);
         for (int i = 0; i < kXRaw; ++i) {
             mbar_init(&raw_full[i], 1);
             mbar_init(&raw_empty[i], kXProducers);
@@ -274,7 +281,8 @@ __global__ void __launch_bounds__(kXThreads, 1) xspec5(Pass p, PassArgs a, const
         bool ok = true;
         for (int n = 0; n < steps && ok; ++n) {
             const int st = n % kXStages, rs = n % kXRaw;
-            ok = __all_sync(0xffffffffu, wait_bar(&raw_full[rs], (n / kXRaw) & 1));
+            ok = __all_sync(0xffffffffu, (a.force_expire && n == 0) ? wait_bar(&never_bar, 0, budget)
+                                                                     : wait_bar(&raw_full[rs], (n / kXRaw) & 1, budget));
             if (!ok) break;
             float4 cur[8];  // samples 8 g + q: (re, im) of frequencies 2 fp, 2 fp + 1
 #pragma unroll
@@ -284,7 +292,7 @@ __global__ void __launch_bounds__(kXThreads, 1) xspec5(Pass p, PassArgs a, const
                                                 raw + (size_t)rs * kRawBytes + ((ts * NT + j) * 2 + fp) * 16)
                                           : make_float4(0.f, 0.f, 0.f, 0.f);
             }
-            if (n >= kXStages) ok = __all_sync(0xffffffffu, wait_bar(&empty[st], (n / kXStages - 1) & 1));
+            if (n >= kXStages) ok = __all_sync(0xffffffffu, wait_bar(&empty[st], (n / kXStages - 1) & 1, budget));
             if (!ok) break;
             unsigned char* stage = dsm + (size_t)st * kStageBytes;
 #pragma unroll
@@ -328,7 +336,7 @@ __global__ void __launch_bounds__(kXThreads, 1) xspec5(Pass p, PassArgs a, const
         int issued = 0;
         for (int n = 0; n < steps && ok; ++n) {
             const int rs = n % kXRaw;
-            if (n >= kXRaw) ok = __all_sync(0xffffffffu, wait_bar(&raw_empty[rs], (n / kXRaw - 1) & 1));
+            if (n >= kXRaw) ok = __all_sync(0xffffffffu, wait_bar(&raw_empty[rs], (n / kXRaw - 1) & 1, budget));
             if (!ok) break;
             unsigned char* slot = dsm + (size_t)kStageRing + (size_t)rs * kRawBytes;
             if (elect_one()) {
@@ -348,7 +356,7 @@ __global__ void __launch_bounds__(kXThreads, 1) xspec5(Pass p, PassArgs a, const
         bool ok = true;
         for (int n = 0; n < steps && ok; ++n) {
             const int st = n % kXStages;
-            ok = __all_sync(0xffffffffu, wait_bar(&full[st], (n / kXStages) & 1));
+            ok = __all_sync(0xffffffffu, wait_bar(&full[st], (n / kXStages) & 1, budget));
             if (!ok) break;
             tc_after_sync();
             unsigned char* stage = dsm + (size_t)st * kStageBytes;

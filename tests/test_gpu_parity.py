@@ -404,6 +404,24 @@ def test_expired_tensor_core_wait_is_reported(monkeypatch):
     assert np.isfinite(V).all()
 
 
+@pytest.mark.parametrize("precision", ["mixed", "mixed_bf16"])
+def test_expired_lag_sum_wait_is_reported(monkeypatch, precision):
+    """The lag-sum kernel's bounded waits: with the test hook its converters wait for
+    a phase that never comes (budget ~0.5 ms), every CTA gives up, drains its copies,
+    frees its tensor memory and sets the error word; the host reports OMNI_ERR_TIMEOUT
+    and the next plan on the same context is correct."""
+    w = synth.workload("hier2")
+    x = synth.voltages(w, channels=2, samples=40)
+    monkeypatch.setenv("OMNI_TEST_FORCE_TIMEOUT", "1")
+    with omni.Plan(w.levels, 2, dtype="ci8", precision=precision) as plan:
+        plan.correlate(x.cuda())
+        with pytest.raises(omni.OmniError) as e:
+            plan.visibilities()
+        assert e.value.status == 6
+    monkeypatch.delenv("OMNI_TEST_FORCE_TIMEOUT")
+    check(w.levels, x, dtype="ci8", tol=TOL_MIXED, precision=precision)
+
+
 @pytest.mark.parametrize("precision, overlap", [("fp32", "1"), ("mixed", "1"), ("mixed", "0")])
 def test_correlate_replays_from_a_cuda_graph(precision, overlap, monkeypatch):
     """omni_correlate (with and without the two streams of overlapped chunk
