@@ -152,6 +152,7 @@ class ClockSampler:
 # kernel sources behind each pass kind (plus the shared headers)
 _PASS_SOURCES = [("lagsum-tcgen05", ("omni_xspec5.cu",)), ("xspec-tcgen05", ("omni_xspec5.cu",)),
                  ("xspec", ("omni_tiles.cu",)), ("tcgen05", ("omni_tc5.cu",)), ("tc", ("omni_tc.cu",)),
+                 ("smem3x", ("omni_fft_smem3.cu",)),
                  ("level", ("omni_fft_level.cuh", "omni_fft_level_a.cu", "omni_fft_level_b.cu")),
                  ("smem", ("omni_fft_smem.cuh", "omni_fft_smem_a.cu", "omni_fft_smem_b.cu",
                            "omni_fft_smem_c.cu")),
