@@ -360,6 +360,13 @@ void choose_level(Pass& p) {
 // Passes of 2048 and 4096 points: the three-step kernel (16-point register
 // transforms; the four-step split 64 x 32 or 64 x 64 held a 64-point column in
 // registers: 210-255 registers per thread, one or two CTAs per SM).
+// Four-step passes along the innermost axis (inner == 1) other than LAST: W
+// consecutive outer lines per CTA (256 threads) instead of one line per CTA of
+// L1 threads.
+void rows_lines(Pass& p) {
+    if (p.kind == KIND_SMEM && p.inner == 1 && p.mode != MODE_LAST) p.W = 256 / p.L1;
+}
+
 void use_smem3(Pass& p, const Knobs& k) {
     if (!k.fft3 || p.kind != KIND_SMEM || !smem3_supports(p.L)) return;
     const bool fwd = p.mode == MODE_MID || p.mode == MODE_LAST;
@@ -439,6 +446,7 @@ omni_status build_passes(omni_plan* pl) {
                 } else {
                     choose_kind(q);
                     if (q.n == q.L && q.L > 1 && q.kind == KIND_SMEM) q.kind = KIND_DIRECT;
+                    rows_lines(q);
                     use_smem3(q, pl->knobs);
                 }
                 level1.push_back(q);
@@ -513,6 +521,7 @@ omni_status build_passes(omni_plan* pl) {
             // unpadded (beam) axes: full-length register FFTs up to 64 points,
             // direct DFTs otherwise (the shared-memory kernels assume padding)
             if (p.n == p.L && p.L > 1 && p.kind == KIND_SMEM) p.kind = KIND_DIRECT;
+            rows_lines(p);
             use_smem3(p, pl->knobs);
         }
         if (p.mode == MODE_MID) pl->fwd_elems = std::max(pl->fwd_elems, p.outer * p.q_out * p.inner);
@@ -564,6 +573,7 @@ omni_status build_passes(omni_plan* pl) {
         if (pl->n_tiles) p.outer *= pl->n_tiles * pl->n_tiles;
         p.mode = (a == 0) ? MODE_INV_LAST : MODE_INV_MID;
         choose_kind(p);
+        rows_lines(p);
         use_smem3(p, pl->knobs);
         if (p.mode == MODE_INV_MID) pl->inv_elems = std::max(pl->inv_elems, p.outer * p.q_out * p.inner);
         pl->inv.push_back(p);

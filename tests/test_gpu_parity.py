@@ -212,6 +212,16 @@ def test_degenerate_and_odd_shapes(levels):
     check(levels, x)
 
 
+@pytest.mark.parametrize("n1, n2", [(64, 3), (3, 64), (256, 2), (2, 512), (128, 8), (60, 70)])
+def test_four_step_axes_rows_and_columns(n1, n2):
+    """Axes of 64..512 antennas (padded 128..1024, four-step passes): along the
+    innermost axis W whole lines per CTA (forward and inverse), strided axes W
+    inner indices per CTA."""
+    levels = [synth.Level(n1, n2, (1.0, 0.1, 0.0, 1.0))]
+    x = synth.random_complex([n1, n2], 2, 3, seed=79)
+    check(levels, x)
+
+
 @pytest.mark.parametrize("n1, n2", [(2048, 2), (2, 2048), (1024, 3), (3, 1024)])
 def test_long_axes_three_step_passes(n1, n2):
     """Axes of 2048 and 1024 antennas (padded to 4096 and 2048): the forward
