@@ -348,8 +348,7 @@ omni_status omni_sum_groups(const double* vis_dev, int64_t C, int64_t Q, const i
  * OMNI_ERR_UNSUPPORTED with the sizes in omni_last_error().
  *
  * The first call on each device does the set-up (uploads the twiddle tables
- * and looks up the array's device address); make that first call before any
- * stream capture begins.  Every call also copies the direct-DFT twiddles
+ * and looks up the array's device address).  Every call also copies the direct-DFT twiddles
  * (when the lattice has a non-power-of-two axis) from host memory and
  * synchronises stream before returning.  Every call shares the one array and
  * the accumulator is cleared at the start of each call: calls that overlap on
