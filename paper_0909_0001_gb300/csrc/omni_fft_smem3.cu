@@ -12,8 +12,8 @@
 // The inverse passes use the same transform (the inverse runs as a forward FFT)
 // on all L inputs and keep the lag slots, the last one conjugated and scaled.
 // A CTA transforms W lines held in shared memory as [j1][j2][j3] with a row pitch
-// L3 + 1, a j1 pitch = 8 and a line pitch = 2 (mod 16) float2, so that each step's
-// half-warps touch 16 different bank pairs; each thread reads one twiddle w^j from
+// L3 + 1, a j1 pitch = 8 and a line pitch = 16 / W (mod 16) float2, so that each
+// step's half-warps touch 16 different bank pairs; each thread reads one twiddle w^j from
 // a shared-memory table (LAST: through L1) and forms the powers it needs in
 // registers.  LAST runs two 256-thread CTAs per SM and, reading the scratch
 // buffer, copies the next sample's inputs asynchronously (cp.async) into a staging
