@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(s3_threads<MODE>(), 512 / s3_threads<MODE>()) 
         for (int m = tid; m < L; m += kS3Threads) tw[m] = g_tw4096[m * (kTwiddleN / L)];
     auto twv = [&](int m) { return TWG ? __ldg(&g_tw4096[m * (kTwiddleN / L)]) : tw[m]; };
 
-    const int n = p.n;  // inputs per line (<= L / 2)
+    const int n = p.n;  // inputs per line (<= L / 2 forward, <= L inverse)
     const int64_t inner = p.inner;
     int64_t b = blockIdx.x, o0 = 0, i0 = 0, s_first = 0, n_samples = 1, cc = 0;
     if constexpr (ROWS) {  // W consecutive outer lines (inner == 1), one sample
@@ -303,21 +303,21 @@ __global__ void __launch_bounds__(s3_threads<MODE>(), 512 / s3_threads<MODE>()) 
                         a.V[(a.c0 + s) * a.V_stride + at] = make_double2((double)x.x * a.scale, -(double)x.y * a.scale);
                 }
             } else {
-            float2* d = a.dst + s * a.dst_stride;
-            for (int e = tid; e < W * L; e += kS3Threads) {
-                int w, k;
-                if constexpr (ROWS) {
-                    w = e / L;
-                    k = e - w * L;
-                } else {
-                    k = e / W;
-                    w = e - k * W;
+                float2* d = a.dst + s * a.dst_stride;
+                for (int e = tid; e < W * L; e += kS3Threads) {
+                    int w, k;
+                    if constexpr (ROWS) {
+                        w = e / L;
+                        k = e - w * L;
+                    } else {
+                        k = e / W;
+                        w = e - k * W;
+                    }
+                    if (!line_ok(w)) continue;
+                    const float2 x = lines[w * PLANE + out_at(k)];
+                    if constexpr (ROWS) d[(o0 + w) * (int64_t)L + k] = x;
+                    else d[o0 * (int64_t)L * inner + (int64_t)k * inner + i0 + w] = x;
                 }
-                if (!line_ok(w)) continue;
-                const float2 x = lines[w * PLANE + out_at(k)];
-                if constexpr (ROWS) d[(o0 + w) * (int64_t)L + k] = x;
-                else d[o0 * (int64_t)L * inner + (int64_t)k * inner + i0 + w] = x;
-            }
             }
         }
         __syncthreads();
